@@ -11,7 +11,7 @@ import numpy as np
 
 from . import build as _build
 
-GMAX = 18
+GMAX = 8
 FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 
 

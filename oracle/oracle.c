@@ -33,8 +33,8 @@
  *   of the previous step (zero at solid nodes, zero before the first step);
  *   alpha is set from M_phi at reference pressure p = 0;
  *   bilinear corners of x_F that are solid are dropped and the remaining
- *   weights renormalised; with no fluid corner the ghost takes the mean of
- *   its fluid lattice neighbours;
+ *   weights renormalised; with no fluid corner the ghost takes the color of
+ *   its fluid lattice neighbour most aligned with n_s;
  *   D3Q19 (not in the paper): same equations with the D3Q19 velocities and
  *   weights, chi_i = (1-alpha) w_i/(1-w_0), and an orthogonal M from
  *   Gram-Schmidt over monomials whose five traceless second-order rows relax
@@ -55,7 +55,7 @@
 #include <string.h>
 
 #define QMAX 19
-#define GMAX 18            /* corners per ghost: 8 (trilinear) or <= 18 fallback neighbours */
+#define GMAX 8             /* corners per ghost: 4 (bilinear) or 8 (trilinear) */
 #define NPHI_FLOOR 1e-6    /* |grad phi| below which n_phi shrinks linearly to 0 */
 
 typedef struct {
@@ -454,13 +454,20 @@ static void build_ghost_entry(orc_sim* s, int64_t g) {
     if (nc > 0 && wsum > 0) {
         for (int k = 0; k < nc; ++k) wt[k] /= wsum;
     } else {
-        /* no fluid corner: mean over the fluid lattice neighbours of the ghost */
-        nc = 0;
+        /* no fluid corner: the fluid lattice neighbour most aligned with n_s
+         * (largest c_i . n_s; a tie goes to the smaller node index) */
+        int64_t best = -1;
+        double best_dot = -INFINITY;
         for (int i = 1; i < s->L.Q; ++i) {
             int64_t y = neighbour(s, s->g_node[g], i, +1);
-            if (s->cls[y] == 0) cor[nc++] = y;
+            if (s->cls[y] != 0) continue;
+            double dot = 0;
+            for (int a = 0; a < 3; ++a) dot += s->L.c[i][a] * s->g_n[3 * g + a];
+            if (dot > best_dot || (dot == best_dot && y < best)) { best_dot = dot; best = y; }
         }
-        for (int k = 0; k < nc; ++k) wt[k] = 1.0 / nc;
+        nc = 1;
+        cor[0] = best;
+        wt[0] = 1.0;
         s->n_fallback++;
     }
     s->g_nc[g] = nc;
