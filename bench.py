@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the fused color-gradient wetting step on GB300.
+
+Workload: D3Q19 192^3, solid sphere R = 32 at the box centre, drop R0 = 24 on
+its +z pole placed at the contact angle (60 deg by default), density ratio 1000,
+viscosity ratio 100, sigma = 0.005, FP32, all axes periodic.  One step = one
+full time step of the hot path (ghost update, fused collide/segregate/stream
+kernel, color kernel) over the whole grid.  MLUPS counts every node of the grid
+(solid included), as the paper's Eq. (MLUPSDefinition).
+
+With torchrun (N > 1) every rank runs an independent case (the next contact
+angle of the sweep 30..150 deg) -- replicas with no collective on the data path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline at <=0.5 deg contact-angle error; served p50/p99 latency"
+THETA_SWEEP = [60.0, 30.0, 90.0, 120.0, 150.0]
+N_GRID, R_SPHERE, R_DROP = 192, 32.0, 24.0
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_step_d3q19_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--n", type=int, default=N_GRID)
+    ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.file.read())) if len(r) >= 9]
+        self.file.close()
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            v = json.load(f).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_launch.cuh"):
+        with open(os.path.join(ROOT, "paper_2605_30878_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(fluid_nodes):
+    """DRAM bytes per k_step launch from the committed ncu summary, scaled to
+    this launch's fluid nodes; None if the kernel source changed since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_hash") != kernel_source_hash():
+        return None
+    return rec["dram_bytes_per_fluid_node"] * fluid_nodes
+
+
+def k_step_bytes_per_fluid_node(Q, D, s, contrast):
+    """Algorithmic bytes of one k_step launch per fluid node: pull N and B (2Q s),
+    write N* and B* (2Q s), read phi (s), read the previous u (D s, only with a
+    density contrast), write u (D s) and p (s), read the node class (1)."""
+    return 4 * Q * s + s + (D * s if contrast else 0) + D * s + s + 1
+
+
+def workload(theta, precision, n=N_GRID):
+    from paper_2605_30878_gb300 import workloads as wl
+    scale = n / float(N_GRID)
+    return wl.sphere_config(n=n, R=R_SPHERE * scale, R0=R_DROP * scale, theta_deg=theta, rho_ratio=1000.0,
+                            mu_ratio=100.0, sigma=0.005, precision=precision)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def time_oracle(cfg, min_seconds, max_steps, warmup=1):
+    import oracle
+    o = oracle.Oracle(cfg["params"], cfg["solid"], cfg["ghosts"])
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    o.step(warmup)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    nn = cfg["solid"].size
+    return nn * steps / dt / 1e6, steps, dt
+
+
+def cores_used():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each timed step is one full
+    oracle time step of a scaled replica of the workload (same geometry ratios
+    and physics), sized so warm-up + timed steps take about two minutes."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    theta = args.theta if args.theta is not None else THETA_SWEEP[0]
+    probe_cfg = workload(theta, 1, n=32)
+    rate32, _, _ = time_oracle(probe_cfg, 0.5, 3)
+    budget_s = 120.0
+    n_ref = int((budget_s * rate32 * 1e6 / max(1, args.steps + args.warmup)) ** (1.0 / 3.0))
+    n_ref = max(24, min(N_GRID, n_ref - n_ref % 8))
+    cfg = workload(theta, 1, n=n_ref)
+    import oracle
+    o = oracle.Oracle(cfg["params"], cfg["solid"], cfg["ghosts"])
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    nn = n_ref ** 3
+    value = nn * args.steps / dt / 1e6
+    sample = ("D3Q19 %d^3 replica of the 192^3 drop-on-sphere workload (sphere R=%.1f, drop R0=%.1f, theta=%g deg, "
+              "density ratio 1000), %d oracle steps after %d warm-up" % (n_ref, R_SPHERE * n_ref / N_GRID,
+                                                                          R_DROP * n_ref / N_GRID, theta,
+                                                                          args.steps, args.warmup))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "D3Q19 192^3 drop on sphere (oracle on a scaled replica)", "grid_ref": n_ref,
+                       "theta_deg": theta, "rho_ratio": 1000.0, "mu_ratio": 100.0, "sigma": 0.005},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+
+    from paper_2605_30878_gb300 import build as lib_build
+    from paper_2605_30878_gb300 import lbm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    lib_build.build()
+    theta = args.theta if args.theta is not None else THETA_SWEEP[rank % len(THETA_SWEEP)]
+    cfg = workload(theta, lbm.FP32, n=args.n)
+    P = cfg["params"]
+    n = args.n
+    nn = n ** 3
+    probe = lbm.make_probe(1, (n / 2.0, n / 2.0, n / 2.0), R_SPHERE * n / N_GRID, (0, 0, 1), 6.0)
+    ng = len(cfg["ghosts"][0])
+
+    dom = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
+    fluid = dom.fluid_nodes()
+    dom.init_droplet(cfg["drop_center"], cfg["R0"])
+    dom.step(args.warmup)
+    dom.sync()
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    start.record(stream)
+    dom.step(args.steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    dom.sync()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = nn * args.steps * world / (ms * 1e-3) / 1e6
+    diag32 = dom.diagnostics(probe)
+
+    # dominant kernel timed kernel by kernel with CUDA events on the same stream
+    prof_steps = max(3, min(args.steps, 60))
+    kms = dom.profile_steps(prof_steps)
+    t_step = kms[1] / prof_steps * 1e-3
+    s, Q, D = 4, 19, 3
+    kb = k_step_bytes_per_fluid_node(Q, D, s, True) * fluid
+    achieved = kb / t_step / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = recorded_traffic(fluid)
+    share = kms / kms.sum()
+    launches = dom.launches_per_step()
+    bytes_step = dom.bytes_per_fluid_node()
+    dom.close()
+    del dom
+    torch.cuda.empty_cache()
+
+    line = None
+    if rank == 0:
+        angle = {"set_deg": theta, "fp32_deg": math.degrees(diag32["contact_angle"]),
+                 "after_steps": args.warmup + args.steps, "max_u": diag32["max_u"]}
+        if not args.no_fp64_check:
+            d64 = lbm.Domain(dict(P, precision=lbm.FP64), cfg["solid"], cfg["ghosts"])
+            d64.init_droplet(cfg["drop_center"], cfg["R0"])
+            d64.step(args.warmup + args.steps)
+            diag64 = d64.diagnostics(probe)
+            d64.close()
+            del d64
+            torch.cuda.empty_cache()
+            angle["fp64_deg"] = math.degrees(diag64["contact_angle"])
+            angle["fp32_vs_fp64_deg"] = abs(angle["fp32_deg"] - angle["fp64_deg"])
+
+        # end to end through the C ABI from host buffers: create (host mask and ghost
+        # list -> device), init, K steps, diagnostics (device -> host), destroy
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        de = lbm.Domain(P, cfg["solid"], cfg["ghosts"], workspace="library")
+        de.init_droplet(cfg["drop_center"], cfg["R0"])
+        de.step(args.steps)
+        de.diagnostics(probe)
+        de.close()
+        e2e_s = time.perf_counter() - t0
+        h2d = nn + ng * (4 + 8 * 4 + 8 * s)
+        d2h = 32 * 8 + 4
+
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            rate, st, dt = time_oracle(cfg, 10.0, 6)
+            cpu = {"value": rate, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
+                   "sample": "%d FP64 oracle steps of the %d^3 workload after 1 warm-up step (%.1f s)" % (st, n, dt)}
+
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "D3Q19 %d^3 drop on sphere: sphere R=%g at the centre, drop R0=%g on the +z pole "
+                                   "at theta=%g deg, rho_l/rho_g=1000, mu_l/mu_g=100, sigma=0.005, FP32, periodic"
+                                   % (n, R_SPHERE * n / N_GRID, R_DROP * n / N_GRID, theta),
+                       "nodes": nn, "fluid_nodes": fluid, "ghost_nodes": ng,
+                       "l2": "inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (lbm.domain_bytes(P, ng) / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": "k_step<19,float,contrast>", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "bytes_per_fluid_node": k_step_bytes_per_fluid_node(Q, D, s, True),
+                         "avg_launch_ms": t_step * 1e3,
+                         "kernel_share": {"ghost": share[0], "step": share[1], "phi": share[2]}},
+            "step_bytes_per_fluid_node": bytes_step,
+            "step_effective_gbs": bytes_step * fluid * args.steps * world / (ms * 1e-3) / 1e9 / world,
+            "mlups_fluid_nodes": fluid * args.steps * world / (ms * 1e-3) / 1e6,
+            "cpu_baseline": cpu,
+            "e2e": {"value": nn * args.steps / e2e_s / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps, "seconds": e2e_s},
+            "gpu_launches": launches * args.steps,
+            "clocks": clk,
+            "contact_angle": angle,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * lbm.h -- C ABI of the GB300 color-gradient lattice Boltzmann wetting step.
+ *
+ * The library advances a two-phase color-gradient lattice Boltzmann model
+ * (D2Q9 as in Appendix A of Bhattacharya et al., arXiv 2605.30878, or its
+ * D3Q19 extension) with the ghost-node wetting boundary condition of
+ * Eq. (ghost-nodePrescription) on staircase solids of any shape.  Every step
+ * of the time integration runs in CUDA kernels for sm_103a; nothing here
+ * falls back to the CPU.
+ *
+ * Conventions shared by every call:
+ *   - node index      node = x + nx*(y + ny*z), 0 <= x < nx, ...; nz = 1 in 2D
+ *   - lattice units   dx = dt = 1, c_s^2 = 1/3 (Appendix A)
+ *   - host arrays     owned by the caller, read or written during the call only
+ *   - device memory   owned by the library, or carved from a caller workspace
+ *   - errors          no call aborts or throws; each returns an lbm_status and
+ *                     lbm_last_error() gives a one-line message.  Device-side
+ *                     failures (non-finite values) are latched on the device
+ *                     and reported by the next synchronising call
+ *                     (lbm_diagnostics, lbm_read_state, lbm_sync).
+ *   - threads         one host thread per domain at a time
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_domain lbm_domain;      /* opaque */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,          /* invalid argument, mask or ghost list */
+    LBM_ERR_OOM = -2,          /* device allocation failed or workspace too small */
+    LBM_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    LBM_ERR_UNSTABLE = -4,     /* a step produced a non-finite velocity or color */
+    LBM_ERR_TIMEOUT = -5,      /* reserved for bounded device waits */
+    LBM_ERR_UNSUPPORTED = -6   /* valid request this build does not implement */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 } lbm_lattice;
+
+/* Arithmetic and storage type of the whole step. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1 } lbm_precision;
+
+/* Physical and numerical parameters (lattice units).  The model of Sec. II
+ * and Appendix A: phi = 1 is the liquid (heavier) phase, phi = 0 the gas;
+ * rho = rho_l phi + rho_g (1-phi), 1/nu = phi/nu_l + (1-phi)/nu_g with
+ * nu_k = mu_k/rho_k, tau = 1/2 + nu/c_s^2.  Interface mobility M_phi fixes
+ * the rest color weight alpha (Appendix A, taken at reference pressure 0).
+ * W >= 4 (Eq. ghost-nodePrescription keeps |eps| <= 1).  theta is the
+ * contact angle measured through the liquid (Eq. sharpWettingCondition).  A
+ * non-periodic axis must have solid nodes on both end layers. */
+typedef struct {
+    int32_t lattice;        /* lbm_lattice */
+    int32_t nx, ny, nz;     /* grid; nz = 1 for D2Q9 */
+    uint32_t periodic;      /* bit0 x, bit1 y, bit2 z */
+    int32_t precision;      /* lbm_precision */
+    double rho_l, rho_g;    /* phase densities, > 0 */
+    double mu_l, mu_g;      /* dynamic viscosities, > 0 */
+    double sigma;           /* surface tension, Eq. (surfaceTensionForce) */
+    double W;               /* interface width */
+    double M_phi;           /* interface mobility, 0 < M_phi (alpha in (0,1)) */
+    double theta;           /* contact angle, radians */
+    double g[3];            /* body acceleration; F_b = rho g */
+} lbm_params;
+
+/* One solid boundary node (a solid node with at least one fluid neighbour
+ * in the lattice stencil, Sec. I) and its unit normal pointing out of the
+ * solid into the fluid (Fig. 2).  In 2D n[2] must be 0. */
+typedef struct {
+    int64_t node;
+    double n[3];
+} lbm_ghost;
+
+/* Optional analytic description of the solid surface, used only by
+ * lbm_diagnostics to measure the contact angle and the apex height. */
+typedef struct {
+    int32_t kind;           /* 0 none, 1 circle (2D) / sphere (3D), 2 plane */
+    int32_t reserved;
+    double center[3];       /* circle/sphere centre, or a point on the plane near the drop */
+    double radius;          /* circle/sphere radius */
+    double normal[3];       /* plane: unit normal out of the solid; circle/sphere: apex axis */
+    double exclude;         /* interface points closer than this to the surface are not fitted */
+} lbm_probe;
+
+/* Reductions over fluid nodes, accumulated in FP64 on the device. */
+typedef struct {
+    double phi_sum;         /* sum of phi: liquid volume (area in 2D) */
+    double mass_liquid;     /* rho_l * sum phi */
+    double mass_gas;        /* rho_g * sum (1 - phi) */
+    double pop_sum;         /* sum of all N_i: equals the fluid node count after each step */
+    double max_u;           /* max |u| (spurious currents at rest) */
+    double p_in, p_out;     /* mean p_h = rho p over nodes with phi > 1-1e-3 / phi < 1e-3 */
+    double fit_center[3];   /* least-squares circle/sphere through the phi = 1/2 crossings */
+    double fit_radius;
+    double contact_angle;   /* radians, from the fit and the probe surface; NaN without probe */
+    double apex;            /* max over phi = 1/2 crossings of (x - center).normal */
+    int64_t n_in, n_out, n_iface, n_fit, n_fluid;
+    int64_t step;           /* steps taken since the last init */
+    int32_t nan_flag;       /* 1 if any fluid node holds a non-finite value */
+    int32_t reserved;
+} lbm_diag;
+
+/* State fields for lbm_read_state / lbm_write_state (host arrays of doubles). */
+typedef enum {
+    LBM_FIELD_N = 0,        /* [Q][nodes]  color-blind populations after streaming */
+    LBM_FIELD_B = 1,        /* [Q][nodes]  liquid-phase populations after streaming */
+    LBM_FIELD_PHI = 2,      /* [nodes]     color; ghost nodes hold their last ghost value */
+    LBM_FIELD_U = 3,        /* [3][nodes]  velocity of the last step, 0 at solid nodes */
+    LBM_FIELD_P = 4         /* [nodes]     auxiliary pressure p = p_h/rho of the last step */
+} lbm_field;
+
+/* Device bytes a domain with these parameters and n_ghosts ghost nodes
+ * needs (state, ghost table and reduction scratch); 0 if the parameters are
+ * invalid.  Use it to size a caller workspace or to admit work. */
+size_t lbm_domain_bytes(const lbm_params* params, int64_t n_ghosts);
+
+/* Create a domain (Sec. II-III).  solid: host uint8[nx*ny*nz], nonzero =
+ * solid.  ghosts: host array listing every solid node with a fluid stencil
+ * neighbour exactly once, with unit normals (|n| within 1e-6 of 1).  The
+ * library computes, in FP64, each ghost's fluid point x_F = x_G + n
+ * (Fig. 2) and its bilinear (2D) / trilinear (3D) weights over the fluid
+ * corners of the cell holding x_F, renormalised; a ghost with no fluid
+ * corner uses its fluid stencil neighbour most aligned with n.
+ * dev_workspace: NULL to let the library allocate, else a device pointer of
+ * ws_bytes >= lbm_domain_bytes(...) that the caller keeps alive until
+ * lbm_destroy.  cuda_stream: cudaStream_t every device call is issued on
+ * (NULL = default stream).  Errors: LBM_ERR_ARG (parameters, mask or ghost
+ * list), LBM_ERR_OOM, LBM_ERR_CUDA.  On error *out is NULL. */
+lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid,
+                             const lbm_ghost* ghosts, int64_t n_ghosts,
+                             void* dev_workspace, size_t ws_bytes,
+                             void* cuda_stream, lbm_domain** out);
+
+/* Initial state with a circular/spherical drop (Eq. equilibriumPhaseField):
+ * phi = (1 + tanh(2 (R0 - |x - centre|)/W))/2 at fluid nodes, |x - centre|
+ * taken to the nearest periodic image on periodic axes; ghost nodes hold
+ * (1 + cos theta)/2 (Sec. III); N_i = chi_i (the equilibrium at u = 0,
+ * p = 0), B_i = phi N_i; u = 0, p = 0.  Asynchronous on the domain stream. */
+lbm_status lbm_init_droplet(lbm_domain* dom, const double centre[3], double R0);
+
+/* Same initial state from a host color field phi[nodes] (values at solid
+ * nodes are ignored). */
+lbm_status lbm_init_phi(lbm_domain* dom, const double* phi_host);
+
+/* Advance n >= 0 time steps, asynchronously on the domain stream.  One step:
+ * ghost update, Eq. (ghost-nodePrescription); at every fluid node the
+ * isotropic stencils of phi (and of the previous velocity), the forces of
+ * Eqs. (surfaceTensionForce), (pressCorrection), (viscCorrection),
+ * (totalForce), the fields of Eqs. (velUpdate), (pressureUpdate), the
+ * collision of Eq. (MRTCOLL) with Eq. (forceGuo), the segregation of Eq.
+ * (segragationStepBlue); streaming, Eqs. (propTotal), (propBlue), with
+ * halfway bounce-back at solid neighbours; the color of Eq. (phiUpdate).
+ * The steps are replayed from a captured CUDA graph.  Errors: LBM_ERR_ARG
+ * (n < 0), LBM_ERR_CUDA. */
+lbm_status lbm_step(lbm_domain* dom, int64_t n);
+
+/* Wait for the domain stream; LBM_ERR_UNSTABLE if a step since the last
+ * check produced a non-finite velocity or color. */
+lbm_status lbm_sync(lbm_domain* dom);
+
+/* Reductions of the current state (see lbm_diag); probe may be NULL.
+ * Synchronises the domain stream. */
+lbm_status lbm_diagnostics(lbm_domain* dom, const lbm_probe* probe, lbm_diag* out);
+
+/* Copy one state field to / from a host double array laid out as in
+ * lbm_field (FP32 domains convert).  read synchronises; write is ordered
+ * before later work on the domain stream and returns after the copy. */
+lbm_status lbm_read_state(lbm_domain* dom, int32_t field, double* host_out);
+lbm_status lbm_write_state(lbm_domain* dom, int32_t field, const double* host_in);
+
+/* Instrumented stepping: advance n >= 1 steps launching the three kernels one
+ * by one (no graph) with CUDA events around each, and add to kernel_ms[0..2]
+ * the milliseconds spent in the ghost update, the fused step kernel and the
+ * color kernel.  Same arithmetic and results as lbm_step; synchronises. */
+lbm_status lbm_profile_steps(lbm_domain* dom, int64_t n, double kernel_ms[3]);
+
+/* Ghost table as computed by lbm_create_domain: per ghost up to 4 (2D) or
+ * 8 (3D) corner node indices and weights (unused slots: weight 0). */
+lbm_status lbm_ghost_table(lbm_domain* dom, int64_t* corner, double* weight, int32_t* n_corner);
+
+/* Number of ghosts that used the most-aligned-neighbour fallback. */
+int64_t lbm_ghost_fallbacks(const lbm_domain* dom);
+
+/* Kernel launches one lbm_step(dom, 1) issues, and the algorithmic device
+ * bytes one step moves per fluid node (populations, fields, node type). */
+int32_t lbm_launches_per_step(const lbm_domain* dom);
+double  lbm_bytes_per_fluid_node(const lbm_domain* dom);
+int64_t lbm_fluid_nodes(const lbm_domain* dom);
+
+/* Message of the last failed call on dom, or of the last failed
+ * lbm_create_domain when dom is NULL. */
+const char* lbm_last_error(const lbm_domain* dom);
+
+/* Free the domain and any device memory the library allocated. */
+void lbm_destroy(lbm_domain* dom);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,736 @@
+// Host side of the C ABI declared in include/lbm.h: validation, ghost-table
+// preparation (x_F = x_G + n_s, Fig. 2), device memory layout, CUDA-graph
+// step replay, state transfer and diagnostics.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lbm.h"
+#include "lbm_launch.cuh"
+
+using namespace lbmgpu;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t ALIGN = 256;
+constexpr int GRAPH_STEPS = 8;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int64_t nn = 0, plane = 0;
+    size_t elem = 0;
+    int Q = 0, D = 0, GK = 0;
+    size_t off_N[2], off_B[2], off_phi, off_u[2], off_p, off_cls, off_gnode, off_gcorner, off_gwt, off_err,
+        off_partial, off_dout;
+    size_t total = 0;
+};
+
+bool make_layout(const lbm_params* P, int64_t ng, Layout& L, std::string& err) {
+    if (!P) { err = "params is NULL"; return false; }
+    if (P->lattice != LBM_D2Q9 && P->lattice != LBM_D3Q19) { err = "lattice must be 9 (D2Q9) or 19 (D3Q19)"; return false; }
+    if (P->precision != LBM_FP32 && P->precision != LBM_FP64) { err = "precision must be LBM_FP32 or LBM_FP64"; return false; }
+    if (P->nx < 1 || P->ny < 1 || P->nz < 1) { err = "grid sizes must be positive"; return false; }
+    if (P->lattice == LBM_D2Q9 && P->nz != 1) { err = "D2Q9 needs nz == 1"; return false; }
+    if (ng < 0) { err = "n_ghosts must be >= 0"; return false; }
+    const int64_t nn = (int64_t)P->nx * P->ny * P->nz;
+    if (nn >= ((int64_t)1 << 31)) { err = "grid has 2^31 nodes or more"; return false; }
+    L.nn = nn;
+    L.plane = (int64_t)round_up((size_t)nn, 64);
+    L.elem = P->precision == LBM_FP64 ? 8 : 4;
+    L.Q = P->lattice;
+    L.D = P->lattice == LBM_D2Q9 ? 2 : 3;
+    L.GK = L.D == 2 ? 4 : 8;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = round_up(o + bytes, ALIGN); return r; };
+    const size_t pop = (size_t)L.Q * L.plane * L.elem;
+    for (int k = 0; k < 2; ++k) { L.off_N[k] = take(pop); L.off_B[k] = take(pop); }
+    L.off_phi = take(L.plane * L.elem);
+    for (int k = 0; k < 2; ++k) L.off_u[k] = take((size_t)L.D * L.plane * L.elem);
+    L.off_p = take(L.plane * L.elem);
+    L.off_cls = take(L.plane);
+    L.off_gnode = take((size_t)(ng + 1) * 4);
+    L.off_gcorner = take((size_t)L.GK * (ng + 1) * 4);
+    L.off_gwt = take((size_t)L.GK * (ng + 1) * L.elem);
+    L.off_err = take(16);
+    L.off_partial = take((size_t)DIAG_MAX_BLOCKS * DG_REC * 8);
+    L.off_dout = take(DG_REC * 8);
+    L.total = o;
+    return true;
+}
+
+}  // namespace
+
+struct lbm_domain {
+    lbm_params prm;
+    Layout lay;
+    bool fp64 = false, contrast = false;
+    char* ws = nullptr;
+    bool own_ws = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int64_t ng = 0, n_fallback = 0, n_fluid = 0;
+    std::vector<uint8_t> h_cls;
+    std::vector<int32_t> h_corner;   // [GK][ng]
+    std::vector<double> h_wt;        // [GK][ng]
+    std::vector<int32_t> h_nc;
+    StepConfig cfg;
+    int cur = 0;                     // buffers holding the current state
+    int64_t step = 0;
+    cudaGraphExec_t g1[2] = {nullptr, nullptr};
+    cudaGraphExec_t g8 = nullptr;
+    std::string err;
+
+    template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
+    void* N(int k) const { return at<void>(lay.off_N[k]); }
+    void* B(int k) const { return at<void>(lay.off_B[k]); }
+    void* U(int k) const { return at<void>(lay.off_u[k]); }
+    void* phi() const { return at<void>(lay.off_phi); }
+    void* p() const { return at<void>(lay.off_p); }
+    uint8_t* cls() const { return at<uint8_t>(lay.off_cls); }
+    int* errflag() const { return at<int>(lay.off_err); }
+};
+
+namespace {
+
+lbm_status fail(lbm_domain* d, lbm_status s, const std::string& msg) {
+    if (d) d->err = msg; else g_create_error = msg;
+    return s;
+}
+
+#define CUDA_TRY(dom, call)                                                                        \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(dom, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+// Lattice neighbour offsets of a stencil (excluding rest), for node classes.
+void stencil_offsets(int Q, std::vector<int>& ox, std::vector<int>& oy, std::vector<int>& oz) {
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int m = std::abs(dx) + std::abs(dy) + std::abs(dz);
+                if (m == 0) continue;
+                if (Q == 9 && dz != 0) continue;
+                if (Q == 19 && m > 2) continue;
+                ox.push_back(dx); oy.push_back(dy); oz.push_back(dz);
+            }
+}
+
+// Color weights chi (Appendix A / Eq. ChiTerm) and alpha from M_phi at p = 0.
+void color_weights(int Q, double M_phi, double chi[19], double& alpha, double& c2chi) {
+    const double cs2 = 1.0 / 3.0;
+    const double w0 = Q == 9 ? 4.0 / 9.0 : 1.0 / 3.0;
+    alpha = 1.0 - 2.0 * M_phi * (1.0 - w0) / cs2;
+    for (int i = 0; i < 19; ++i) chi[i] = 0.0;
+    chi[0] = alpha;
+    for (int i = 1; i < Q; ++i) {
+        const double wi = Q == 9 ? Lattice<9>::w(i) : Lattice<19>::w(i);
+        chi[i] = (1.0 - alpha) * wi / (1.0 - w0);
+    }
+    c2chi = (1.0 - alpha) * cs2 / (1.0 - w0);
+}
+
+lbm_status prepare_ghosts(lbm_domain* d, const lbm_ghost* ghosts) {
+    const lbm_params& P = d->prm;
+    const int D = d->lay.D, GK = d->lay.GK;
+    const int64_t ng = d->ng, nx = P.nx, ny = P.ny, nz = P.nz;
+    const int dims[3] = {P.nx, P.ny, P.nz};
+    d->h_corner.assign((size_t)GK * ng, 0);
+    d->h_wt.assign((size_t)GK * ng, 0.0);
+    d->h_nc.assign(ng, 0);
+    std::vector<int> ox, oy, oz;
+    stencil_offsets(P.lattice, ox, oy, oz);
+    std::vector<uint8_t> seen(d->lay.nn, 0);
+    for (int64_t g = 0; g < ng; ++g) {
+        const int64_t node = ghosts[g].node;
+        if (node < 0 || node >= d->lay.nn || d->h_cls[node] != CLS_GHOST)
+            return fail(nullptr, LBM_ERR_ARG, "ghost " + std::to_string(g) + " (node " + std::to_string(node) +
+                                                  ") is not a solid node with a fluid neighbour");
+        if (seen[node]) return fail(nullptr, LBM_ERR_ARG, "node " + std::to_string(node) + " is listed twice");
+        seen[node] = 1;
+        const double* n = ghosts[g].n;
+        const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(std::fabs(len - 1.0) <= 1e-6))
+            return fail(nullptr, LBM_ERR_ARG, "ghost " + std::to_string(g) + " normal is not a unit vector");
+        if (D == 2 && n[2] != 0.0)
+            return fail(nullptr, LBM_ERR_ARG, "ghost " + std::to_string(g) + " has a z normal on a 2D lattice");
+        const int64_t xyz[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+        // x_F = x_G + n_s; its cell corners and bilinear/trilinear weights
+        double base[3] = {0, 0, 0}, frac[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) {
+            const double xf = (double)xyz[a] + n[a];
+            base[a] = std::floor(xf);
+            frac[a] = xf - base[a];
+        }
+        int kept = 0;
+        double wsum = 0.0;
+        int32_t cidx[8];
+        double cw[8];
+        for (int k = 0; k < (1 << D); ++k) {
+            int64_t c[3] = {0, 0, 0};
+            double wk = 1.0;
+            for (int a = 0; a < D; ++a) {
+                const int bit = (k >> a) & 1;
+                int64_t v = (int64_t)base[a] + bit;
+                v %= dims[a];
+                if (v < 0) v += dims[a];
+                c[a] = v;
+                wk *= bit ? frac[a] : 1.0 - frac[a];
+            }
+            const int64_t cn = c[0] + nx * (c[1] + ny * c[2]);
+            if (d->h_cls[cn] == CLS_FLUID) {
+                cidx[kept] = (int32_t)cn;
+                cw[kept] = wk;
+                wsum += wk;
+                ++kept;
+            }
+        }
+        if (kept > 0 && wsum > 0.0) {
+            for (int k = 0; k < kept; ++k) cw[k] /= wsum;
+        } else {
+            // the fluid stencil neighbour most aligned with n_s; ties -> smaller node index
+            int64_t best = -1;
+            double best_dot = -INFINITY;
+            for (size_t j = 0; j < ox.size(); ++j) {
+                int64_t c[3] = {xyz[0] + ox[j], xyz[1] + oy[j], xyz[2] + oz[j]};
+                for (int a = 0; a < 3; ++a) { c[a] %= dims[a]; if (c[a] < 0) c[a] += dims[a]; }
+                const int64_t cn = c[0] + nx * (c[1] + ny * c[2]);
+                if (d->h_cls[cn] != CLS_FLUID) continue;
+                const double dot = ox[j] * n[0] + oy[j] * n[1] + oz[j] * n[2];
+                if (dot > best_dot || (dot == best_dot && cn < best)) { best_dot = dot; best = cn; }
+            }
+            kept = 1;
+            cidx[0] = (int32_t)best;
+            cw[0] = 1.0;
+            d->n_fallback++;
+        }
+        d->h_nc[g] = kept;
+        for (int k = 0; k < GK; ++k) {
+            d->h_corner[(size_t)k * ng + g] = k < kept ? cidx[k] : cidx[0];
+            d->h_wt[(size_t)k * ng + g] = k < kept ? cw[k] : 0.0;
+        }
+    }
+    (void)nz;
+    return LBM_OK;
+}
+
+// ev: optional events {before ghost, before step, before phi, after phi}
+void launch_one_step(lbm_domain* d, int cur, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+    const Layout& L = d->lay;
+    if (ev) cudaEventRecord(ev[0], s);
+    if (d->ng > 0) {
+        const void* wt = d->at<void>(L.off_gwt);
+        if (d->fp64)
+            Launch<double>::ghost(L.GK, d->ng, d->at<int32_t>(L.off_gnode), d->at<int32_t>(L.off_gcorner), wt,
+                                  d->cfg.exp_eps, d->phi(), s);
+        else
+            Launch<float>::ghost(L.GK, d->ng, d->at<int32_t>(L.off_gnode), d->at<int32_t>(L.off_gcorner), wt,
+                                 d->cfg.exp_eps, d->phi(), s);
+    }
+    StepPtrs sp;
+    sp.Nin = d->N(cur); sp.Bin = d->B(cur); sp.Nout = d->N(1 - cur); sp.Bout = d->B(1 - cur);
+    sp.phi = d->phi(); sp.u_in = d->U(cur); sp.u_out = d->U(1 - cur); sp.p = d->p();
+    sp.cls = d->cls(); sp.err = d->errflag();
+    if (ev) cudaEventRecord(ev[1], s);
+    if (d->fp64) Launch<double>::step(d->cfg, sp, s);
+    else Launch<float>::step(d->cfg, sp, s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if (d->fp64) Launch<double>::phi(d->cfg, d->B(1 - cur), d->cls(), d->phi(), s);
+    else Launch<float>::phi(d->cfg, d->B(1 - cur), d->cls(), d->phi(), s);
+    if (ev) cudaEventRecord(ev[3], s);
+}
+
+lbm_status capture(lbm_domain* d, int start, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(d, cudaStreamBeginCapture(d->cap, cudaStreamCaptureModeThreadLocal));
+    int c = start;
+    for (int k = 0; k < nsteps; ++k) { launch_one_step(d, c, d->cap); c ^= 1; }
+    cudaError_t e = cudaStreamEndCapture(d->cap, &g);
+    if (e != cudaSuccess) return fail(d, LBM_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(d, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status check_err_flag(lbm_domain* d) {
+    int h = 0;
+    CUDA_TRY(d, cudaMemcpyAsync(&h, d->errflag(), sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+    CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    if (h) return fail(d, LBM_ERR_UNSTABLE, "a step produced a non-finite velocity");
+    return LBM_OK;
+}
+
+// host double <-> device T conversions through a staging vector
+lbm_status upload(lbm_domain* d, void* dst, const double* src, size_t count) {
+    if (d->fp64) {
+        CUDA_TRY(d, cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyHostToDevice, d->stream));
+        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    } else {
+        std::vector<float> tmp(count);
+        for (size_t k = 0; k < count; ++k) tmp[k] = (float)src[k];
+        CUDA_TRY(d, cudaMemcpyAsync(dst, tmp.data(), count * 4, cudaMemcpyHostToDevice, d->stream));
+        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status download(lbm_domain* d, double* dst, const void* src, size_t count) {
+    if (d->fp64) {
+        CUDA_TRY(d, cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyDeviceToHost, d->stream));
+        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    } else {
+        std::vector<float> tmp(count);
+        CUDA_TRY(d, cudaMemcpyAsync(tmp.data(), src, count * 4, cudaMemcpyDeviceToHost, d->stream));
+        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+        for (size_t k = 0; k < count; ++k) dst[k] = (double)tmp[k];
+    }
+    return LBM_OK;
+}
+
+lbm_status init_state(lbm_domain* d, int mode, const double ctr[3], double R0) {
+    const double ghost_value = 0.5 * (1.0 + std::cos(d->prm.theta));
+    d->cur = 0;
+    d->step = 0;
+    const Layout& L = d->lay;
+    CUDA_TRY(d, cudaMemsetAsync(d->errflag(), 0, sizeof(int), d->stream));
+    for (int k = 0; k < 2; ++k) {
+        CUDA_TRY(d, cudaMemsetAsync(d->U(k), 0, (size_t)L.D * L.plane * L.elem, d->stream));
+        CUDA_TRY(d, cudaMemsetAsync(d->N(k), 0, (size_t)L.Q * L.plane * L.elem, d->stream));
+        CUDA_TRY(d, cudaMemsetAsync(d->B(k), 0, (size_t)L.Q * L.plane * L.elem, d->stream));
+    }
+    CUDA_TRY(d, cudaMemsetAsync(d->p(), 0, (size_t)L.plane * L.elem, d->stream));
+    if (d->fp64) {
+        Launch<double>::init_phi(d->cfg, d->cls(), d->phi(), mode, ctr, R0, ghost_value, d->stream);
+        Launch<double>::init_pops(d->cfg, d->cls(), d->phi(), d->N(0), d->B(0), d->stream);
+    } else {
+        Launch<float>::init_phi(d->cfg, d->cls(), d->phi(), mode, ctr, R0, ghost_value, d->stream);
+        Launch<float>::init_pops(d->cfg, d->cls(), d->phi(), d->N(0), d->B(0), d->stream);
+    }
+    CUDA_TRY(d, cudaGetLastError());
+    return LBM_OK;
+}
+
+// Solve the (n x n) system A z = b, n <= 4, by Gaussian elimination with partial pivoting.
+bool solve_dense(int n, double A[4][4], double b[4], double z[4]) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return false;
+        if (piv != c) {
+            for (int j = 0; j < n; ++j) std::swap(A[c][j], A[piv][j]);
+            std::swap(b[c], b[piv]);
+        }
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int j = c; j < n; ++j) A[r][j] -= f * A[c][j];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int j = r + 1; j < n; ++j) s -= A[r][j] * z[j];
+        z[r] = s / A[r][r];
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_domain_bytes(const lbm_params* params, int64_t n_ghosts) {
+    Layout L;
+    std::string err;
+    if (!make_layout(params, n_ghosts, L, err)) return 0;
+    return L.total;
+}
+
+lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, const lbm_ghost* ghosts,
+                             int64_t n_ghosts, void* dev_workspace, size_t ws_bytes, void* cuda_stream,
+                             lbm_domain** out) {
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    Layout L;
+    std::string err;
+    if (!make_layout(params, n_ghosts, L, err)) return fail(nullptr, LBM_ERR_ARG, err);
+    const lbm_params& P = *params;
+    if (!solid) return fail(nullptr, LBM_ERR_ARG, "solid mask is NULL");
+    if (n_ghosts > 0 && !ghosts) return fail(nullptr, LBM_ERR_ARG, "ghost list is NULL");
+    if (!(P.W >= 4.0)) return fail(nullptr, LBM_ERR_ARG, "W must be >= 4 lattice units");
+    if (!(P.rho_l > 0 && P.rho_g > 0 && P.mu_l > 0 && P.mu_g > 0))
+        return fail(nullptr, LBM_ERR_ARG, "densities and viscosities must be positive");
+    if (!(P.sigma >= 0)) return fail(nullptr, LBM_ERR_ARG, "sigma must be >= 0");
+    if (!std::isfinite(P.theta) || !std::isfinite(P.g[0]) || !std::isfinite(P.g[1]) || !std::isfinite(P.g[2]))
+        return fail(nullptr, LBM_ERR_ARG, "theta and g must be finite");
+
+    lbm_domain* d = new lbm_domain();
+    d->prm = P;
+    d->lay = L;
+    d->fp64 = P.precision == LBM_FP64;
+    d->contrast = P.rho_l != P.rho_g;
+    d->ng = n_ghosts;
+    d->stream = (cudaStream_t)cuda_stream;
+
+    double alpha, c2chi;
+    StepConfig& c = d->cfg;
+    color_weights(P.lattice, P.M_phi, c.chi, alpha, c2chi);
+    if (!(alpha > 0.0 && alpha < 1.0)) { delete d; return fail(nullptr, LBM_ERR_ARG, "M_phi gives alpha outside (0,1)"); }
+    c.Q = P.lattice;
+    c.contrast = d->contrast;
+    c.d = Dims{P.nx, P.ny, P.nz, L.plane, P.periodic};
+    c.rho_l = P.rho_l; c.rho_g = P.rho_g;
+    c.nu_l = P.mu_l / P.rho_l; c.nu_g = P.mu_g / P.rho_g;
+    c.sigma = P.sigma; c.W = P.W;
+    for (int a = 0; a < 3; ++a) c.g[a] = (L.D == 2 && a == 2) ? 0.0 : P.g[a];
+    c.c2chi = c2chi;
+    c.exp_eps = std::exp(-(4.0 / P.W) * std::cos(P.theta));
+
+    // node classes: a solid node with a fluid stencil neighbour is a ghost
+    const int64_t nn = L.nn;
+    const int64_t nx = P.nx, ny = P.ny, nz = P.nz;
+    d->h_cls.assign(nn, CLS_FLUID);
+    std::vector<int> ox, oy, oz;
+    stencil_offsets(P.lattice, ox, oy, oz);
+    int64_t n_cls_ghost = 0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t node = x + nx * (y + ny * z);
+                if (!solid[node]) { d->n_fluid++; continue; }
+                uint8_t cl = CLS_SOLID;
+                for (size_t j = 0; j < ox.size(); ++j) {
+                    const int64_t xx = (x + ox[j] + nx) % nx, yy = (y + oy[j] + ny) % ny, zz = (z + oz[j] + nz) % nz;
+                    if (!solid[xx + nx * (yy + ny * zz)]) { cl = CLS_GHOST; break; }
+                }
+                d->h_cls[node] = cl;
+                n_cls_ghost += cl == CLS_GHOST;
+            }
+    const int64_t ext[3] = {nx, ny, nz};
+    for (int a = 0; a < L.D; ++a) {
+        if (P.periodic & (1u << a)) continue;
+        for (int64_t node = 0; node < nn; ++node) {
+            const int64_t r[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+            if ((r[a] == 0 || r[a] == ext[a] - 1) && !solid[node]) {
+                delete d;
+                return fail(nullptr, LBM_ERR_ARG, "axis " + std::to_string(a) + " is not periodic but has fluid on an end layer");
+            }
+        }
+    }
+    if (n_cls_ghost != n_ghosts) {
+        delete d;
+        return fail(nullptr, LBM_ERR_ARG, "ghost list has " + std::to_string(n_ghosts) + " entries, mask has " +
+                                              std::to_string(n_cls_ghost) + " ghost nodes");
+    }
+    lbm_status st = prepare_ghosts(d, ghosts);
+    if (st != LBM_OK) { delete d; return st; }
+
+    // device memory
+    if (dev_workspace) {
+        if (ws_bytes < L.total) {
+            delete d;
+            return fail(nullptr, LBM_ERR_OOM, "workspace of " + std::to_string(ws_bytes) + " bytes, need " + std::to_string(L.total));
+        }
+        if (reinterpret_cast<uintptr_t>(dev_workspace) % ALIGN) {
+            delete d;
+            return fail(nullptr, LBM_ERR_ARG, "workspace must be 256-byte aligned");
+        }
+        d->ws = (char*)dev_workspace;
+    } else {
+        void* p = nullptr;
+        if (cudaMalloc(&p, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete d;
+            return fail(nullptr, LBM_ERR_OOM, "cudaMalloc of " + std::to_string(L.total) + " bytes failed");
+        }
+        d->ws = (char*)p;
+        d->own_ws = true;
+    }
+    auto bail = [&](const std::string& m) {
+        std::string msg = m;
+        lbm_destroy(d);
+        return fail(nullptr, LBM_ERR_CUDA, msg);
+    };
+    if (cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking) != cudaSuccess) return bail("cudaStreamCreate failed");
+    // upload node classes and the ghost table
+    std::vector<int32_t> gnode(n_ghosts);
+    for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)ghosts[g].node;
+    cudaStream_t s = d->stream;
+    if (cudaMemsetAsync(d->ws, 0, L.total, s) != cudaSuccess) return bail("cudaMemset failed");
+    if (cudaMemcpyAsync(d->cls(), d->h_cls.data(), nn, cudaMemcpyHostToDevice, s) != cudaSuccess) return bail("upload of node classes failed");
+    if (n_ghosts > 0) {
+        if (cudaMemcpyAsync(d->at<void>(L.off_gnode), gnode.data(), n_ghosts * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(d->at<void>(L.off_gcorner), d->h_corner.data(), d->h_corner.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return bail("upload of the ghost table failed");
+        if (d->fp64) {
+            if (cudaMemcpyAsync(d->at<void>(L.off_gwt), d->h_wt.data(), d->h_wt.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return bail("upload of the ghost weights failed");
+        } else {
+            std::vector<float> wf(d->h_wt.begin(), d->h_wt.end());
+            if (cudaMemcpyAsync(d->at<void>(L.off_gwt), wf.data(), wf.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return bail("upload of the ghost weights failed");
+        }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail("synchronisation after upload failed");
+    if (capture(d, 0, 1, &d->g1[0]) != LBM_OK || capture(d, 1, 1, &d->g1[1]) != LBM_OK ||
+        capture(d, 0, GRAPH_STEPS, &d->g8) != LBM_OK)
+        return bail("CUDA graph capture of the step failed: " + d->err);
+    *out = d;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_droplet(lbm_domain* d, const double centre[3], double R0) {
+    if (!d || !centre) return fail(d, LBM_ERR_ARG, "NULL argument");
+    if (!(R0 > 0) || !std::isfinite(centre[0]) || !std::isfinite(centre[1]) || !std::isfinite(centre[2]))
+        return fail(d, LBM_ERR_ARG, "drop radius must be positive and the centre finite");
+    return init_state(d, 0, centre, R0);
+}
+
+lbm_status lbm_init_phi(lbm_domain* d, const double* phi_host) {
+    if (!d || !phi_host) return fail(d, LBM_ERR_ARG, "NULL argument");
+    lbm_status st = upload(d, d->phi(), phi_host, d->lay.nn);
+    if (st != LBM_OK) return st;
+    const double zero[3] = {0, 0, 0};
+    return init_state(d, 1, zero, 1.0);
+}
+
+lbm_status lbm_step(lbm_domain* d, int64_t n) {
+    if (!d) return fail(d, LBM_ERR_ARG, "NULL domain");
+    if (n < 0) return fail(d, LBM_ERR_ARG, "n must be >= 0");
+    while (n > 0) {
+        if (d->cur == 0 && n >= GRAPH_STEPS) {
+            CUDA_TRY(d, cudaGraphLaunch(d->g8, d->stream));
+            n -= GRAPH_STEPS;
+            d->step += GRAPH_STEPS;
+        } else {
+            CUDA_TRY(d, cudaGraphLaunch(d->g1[d->cur], d->stream));
+            d->cur ^= 1;
+            --n;
+            d->step += 1;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_steps(lbm_domain* d, int64_t n, double kernel_ms[3]) {
+    if (!d || !kernel_ms) return fail(d, LBM_ERR_ARG, "NULL argument");
+    if (n < 1) return fail(d, LBM_ERR_ARG, "n must be >= 1");
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) CUDA_TRY(d, cudaEventCreate(&ev[k]));
+    lbm_status st = LBM_OK;
+    for (int64_t t = 0; t < n && st == LBM_OK; ++t) {
+        launch_one_step(d, d->cur, d->stream, ev);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+        if (e != cudaSuccess) { st = fail(d, LBM_ERR_CUDA, std::string("profiled step: ") + cudaGetErrorString(e)); break; }
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            kernel_ms[k] += ms;
+        }
+        d->cur ^= 1;
+        d->step += 1;
+    }
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+    return st;
+}
+
+lbm_status lbm_sync(lbm_domain* d) {
+    if (!d) return fail(d, LBM_ERR_ARG, "NULL domain");
+    CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    return check_err_flag(d);
+}
+
+lbm_status lbm_diagnostics(lbm_domain* d, const lbm_probe* probe, lbm_diag* out) {
+    if (!d || !out) return fail(d, LBM_ERR_ARG, "NULL argument");
+    const Layout& L = d->lay;
+    ProbeDev pr{};
+    pr.kind = 0;
+    if (probe) {
+        if (probe->kind < 0 || probe->kind > 2) return fail(d, LBM_ERR_ARG, "probe kind must be 0, 1 or 2");
+        pr.kind = probe->kind;
+        for (int a = 0; a < 3; ++a) { pr.center[a] = probe->center[a]; pr.normal[a] = probe->normal[a]; }
+        pr.radius = probe->radius;
+        pr.exclude = probe->exclude;
+    }
+    double* partial = d->at<double>(L.off_partial);
+    double* dout = d->at<double>(L.off_dout);
+    if (d->fp64)
+        Launch<double>::diag(d->cfg, d->cls(), d->N(d->cur), d->phi(), d->U(d->cur), d->p(), pr, partial, dout, d->stream);
+    else
+        Launch<float>::diag(d->cfg, d->cls(), d->N(d->cur), d->phi(), d->U(d->cur), d->p(), pr, partial, dout, d->stream);
+    CUDA_TRY(d, cudaGetLastError());
+    double h[DG_REC];
+    CUDA_TRY(d, cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, d->stream));
+    CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    std::memset(out, 0, sizeof(*out));
+    const lbm_params& P = d->prm;
+    out->phi_sum = h[DG_PHI];
+    out->n_fluid = (int64_t)h[DG_NFLUID];
+    out->mass_liquid = P.rho_l * h[DG_PHI];
+    out->mass_gas = P.rho_g * (h[DG_NFLUID] - h[DG_PHI]);
+    out->pop_sum = h[DG_POP];
+    out->max_u = std::sqrt(h[DG_MAXU2]);
+    out->n_in = (int64_t)h[DG_NIN];
+    out->n_out = (int64_t)h[DG_NOUT];
+    out->p_in = out->n_in ? h[DG_PIN] / h[DG_NIN] : 0.0;
+    out->p_out = out->n_out ? h[DG_POUT] / h[DG_NOUT] : 0.0;
+    out->n_iface = (int64_t)h[DG_NIFACE];
+    out->n_fit = (int64_t)h[DG_NFIT];
+    out->step = d->step;
+    out->nan_flag = h[DG_NAN] > 0 ? 1 : 0;
+    out->contact_angle = NAN;
+    out->apex = NAN;
+    if (pr.kind != 0) {
+        out->apex = h[DG_APEX];
+        const int D = L.D;
+        double A[4][4], b[4], z[4] = {0, 0, 0, 0};
+        for (int i = 0; i <= D; ++i) {
+            for (int j = 0; j <= D; ++j) A[i][j] = h[DG_A + 4 * i + j];
+            b[i] = h[DG_B + i];
+        }
+        if (out->n_fit >= D + 2 && solve_dense(D + 1, A, b, z)) {
+            double c2 = 0.0, hn = 0.0;
+            for (int k = 0; k < D; ++k) {
+                const double ck = -z[k] / 2.0;
+                out->fit_center[k] = ck + pr.center[k];
+                c2 += ck * ck;
+                hn += ck * pr.normal[k];
+            }
+            out->fit_radius = std::sqrt(c2 - z[D]);
+            const double r = out->fit_radius;
+            if (pr.kind == 1) {
+                const double R = pr.radius;
+                out->contact_angle = std::acos((R * R + r * r - c2) / (2.0 * R * r));
+            } else {
+                out->contact_angle = std::acos(-hn / r);
+            }
+        }
+    }
+    lbm_status st = check_err_flag(d);
+    if (out->nan_flag && st == LBM_OK) return fail(d, LBM_ERR_UNSTABLE, "non-finite color or velocity in the state");
+    return st;
+}
+
+lbm_status lbm_read_state(lbm_domain* d, int32_t field, double* host_out) {
+    if (!d || !host_out) return fail(d, LBM_ERR_ARG, "NULL argument");
+    const Layout& L = d->lay;
+    const int64_t nn = L.nn;
+    std::vector<double> tmp;
+    switch (field) {
+    case LBM_FIELD_N:
+    case LBM_FIELD_B: {
+        void* st = field == LBM_FIELD_N ? d->N(d->cur) : d->B(d->cur);
+        void* spare = field == LBM_FIELD_N ? d->N(1 - d->cur) : d->B(1 - d->cur);
+        if (d->fp64) Launch<double>::gather(d->cfg, d->cls(), st, spare, d->stream);
+        else Launch<float>::gather(d->cfg, d->cls(), st, spare, d->stream);
+        CUDA_TRY(d, cudaGetLastError());
+        for (int i = 0; i < L.Q; ++i) {
+            lbm_status s = download(d, host_out + (size_t)i * nn, (const char*)spare + (size_t)i * L.plane * L.elem, nn);
+            if (s != LBM_OK) return s;
+        }
+        return LBM_OK;
+    }
+    case LBM_FIELD_PHI:
+        return download(d, host_out, d->phi(), nn);
+    case LBM_FIELD_U: {
+        for (int a = 0; a < 3; ++a) {
+            if (a < L.D) {
+                lbm_status s = download(d, host_out + (size_t)a * nn, (const char*)d->U(d->cur) + (size_t)a * L.plane * L.elem, nn);
+                if (s != LBM_OK) return s;
+            } else {
+                std::fill(host_out + (size_t)a * nn, host_out + (size_t)(a + 1) * nn, 0.0);
+            }
+        }
+        return LBM_OK;
+    }
+    case LBM_FIELD_P:
+        return download(d, host_out, d->p(), nn);
+    }
+    return fail(d, LBM_ERR_ARG, "unknown field");
+}
+
+lbm_status lbm_write_state(lbm_domain* d, int32_t field, const double* host_in) {
+    if (!d || !host_in) return fail(d, LBM_ERR_ARG, "NULL argument");
+    const Layout& L = d->lay;
+    const int64_t nn = L.nn;
+    switch (field) {
+    case LBM_FIELD_N:
+    case LBM_FIELD_B: {
+        void* st = field == LBM_FIELD_N ? d->N(d->cur) : d->B(d->cur);
+        void* spare = field == LBM_FIELD_N ? d->N(1 - d->cur) : d->B(1 - d->cur);
+        for (int i = 0; i < L.Q; ++i) {
+            lbm_status s = upload(d, (char*)spare + (size_t)i * L.plane * L.elem, host_in + (size_t)i * nn, nn);
+            if (s != LBM_OK) return s;
+        }
+        if (d->fp64) Launch<double>::scatter(d->cfg, d->cls(), spare, st, d->stream);
+        else Launch<float>::scatter(d->cfg, d->cls(), spare, st, d->stream);
+        CUDA_TRY(d, cudaGetLastError());
+        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+        return LBM_OK;
+    }
+    case LBM_FIELD_PHI:
+        return upload(d, d->phi(), host_in, nn);
+    case LBM_FIELD_U:
+        for (int a = 0; a < L.D; ++a) {
+            lbm_status s = upload(d, (char*)d->U(d->cur) + (size_t)a * L.plane * L.elem, host_in + (size_t)a * nn, nn);
+            if (s != LBM_OK) return s;
+        }
+        return LBM_OK;
+    case LBM_FIELD_P:
+        return upload(d, d->p(), host_in, nn);
+    }
+    return fail(d, LBM_ERR_ARG, "unknown field");
+}
+
+lbm_status lbm_ghost_table(lbm_domain* d, int64_t* corner, double* weight, int32_t* n_corner) {
+    if (!d || !corner || !weight || !n_corner) return fail(d, LBM_ERR_ARG, "NULL argument");
+    const int GK = d->lay.GK;
+    for (int64_t g = 0; g < d->ng; ++g) {
+        n_corner[g] = d->h_nc[g];
+        for (int k = 0; k < GK; ++k) {
+            corner[g * GK + k] = d->h_corner[(size_t)k * d->ng + g];
+            weight[g * GK + k] = d->h_wt[(size_t)k * d->ng + g];
+        }
+    }
+    return LBM_OK;
+}
+
+int64_t lbm_ghost_fallbacks(const lbm_domain* d) { return d ? d->n_fallback : 0; }
+
+int32_t lbm_launches_per_step(const lbm_domain* d) { return d ? (d->ng > 0 ? 3 : 2) : 0; }
+
+double lbm_bytes_per_fluid_node(const lbm_domain* d) {
+    if (!d) return 0.0;
+    const double s = (double)d->lay.elem;
+    const int Q = d->lay.Q, D = d->lay.D;
+    // populations read + written twice over (N, B); phi written (k_phi) and read (k_step);
+    // u written, and read when the density contrast makes F_visc active; p written; node class
+    // read by k_step and k_phi
+    return 4.0 * Q * s + 2.0 * s + (d->contrast ? 2.0 : 1.0) * D * s + s + 2.0;
+}
+
+int64_t lbm_fluid_nodes(const lbm_domain* d) { return d ? d->n_fluid : 0; }
+
+const char* lbm_last_error(const lbm_domain* d) { return d ? d->err.c_str() : g_create_error.c_str(); }
+
+void lbm_destroy(lbm_domain* d) {
+    if (!d) return;
+    if (d->g8) cudaGraphExecDestroy(d->g8);
+    for (int k = 0; k < 2; ++k)
+        if (d->g1[k]) cudaGraphExecDestroy(d->g1[k]);
+    if (d->cap) cudaStreamDestroy(d->cap);
+    if (d->own_ws && d->ws) cudaFree(d->ws);
+    delete d;
+}
+
+}  // extern "C"

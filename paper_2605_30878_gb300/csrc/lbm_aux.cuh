@@ -1,0 +1,246 @@
+// Initialisation, state transfer and diagnostics kernels (not on the per-step path).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbmgpu {
+
+struct Dims {
+    int nx, ny, nz;
+    int64_t plane;
+    uint32_t periodic;
+};
+
+__device__ __forceinline__ void node_xyz(int64_t node, const Dims& d, int& x, int& y, int& z) {
+    x = (int)(node % d.nx);
+    y = (int)((node / d.nx) % d.ny);
+    z = (int)(node / ((int64_t)d.nx * d.ny));
+}
+
+__device__ __forceinline__ int64_t shifted(const Dims& d, int x, int y, int z, int dx, int dy, int dz) {
+    const int xx = wrap_any(x + dx, d.nx), yy = wrap_any(y + dy, d.ny), zz = wrap_any(z + dz, d.nz);
+    return xx + (int64_t)d.nx * (yy + (int64_t)d.ny * zz);
+}
+
+// Color at t = 0 (Eq. equilibriumPhaseField and the ghost value of Sec. III).
+// mode 0: drop of radius R0 at centre; mode 1: keep the fluid values already in phi.
+template <int D, typename T>
+__global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restrict__ phi, int mode, double cx,
+                           double cy, double cz, double R0, double W, double ghost_value) {
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t c = cls[node];
+        if (c == CLS_FLUID) {
+            if (mode == 0) {
+                int x, y, z;
+                node_xyz(node, d, x, y, z);
+                const double ctr[3] = {cx, cy, cz};
+                const int n[3] = {d.nx, d.ny, d.nz};
+                const int r[3] = {x, y, z};
+                double d2 = 0.0;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    double v = r[a] - ctr[a];
+                    if (d.periodic & (1u << a)) v -= n[a] * floor(v / n[a] + 0.5);
+                    d2 += v * v;
+                }
+                phi[node] = (T)(0.5 * (1.0 + tanh(2.0 * (R0 - sqrt(d2)) / W)));
+            }
+        } else {
+            phi[node] = (c == CLS_GHOST) ? (T)ghost_value : T(0);
+        }
+    }
+}
+
+// Populations at t = 0: post-streaming N_i = chi_i, B_i = phi chi_i, written in
+// the pull layout (the value a later pull at x + c_i reads sits at x).
+template <int Q, typename T>
+__global__ void k_init_pops(Dims d, StepParams<T> P, const uint8_t* __restrict__ cls, const T* __restrict__ phi,
+                            T* __restrict__ Nst, T* __restrict__ Bst) {
+    using L = Lattice<Q>;
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        if (cls[node] != CLS_FLUID) continue;
+        int x, y, z;
+        node_xyz(node, d, x, y, z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int64_t dn = shifted(d, x, y, z, L::cx(i), L::cy(i), L::cz(i));
+            const T ph = (cls[dn] == CLS_FLUID) ? phi[dn] : phi[node];
+            Nst[i * d.plane + node] = P.chi[i];
+            Bst[i * d.plane + node] = ph * P.chi[i];
+        }
+    }
+}
+
+// post-streaming values -> pull layout (inverse of k_gather)
+template <int Q, typename T>
+__global__ void k_scatter(Dims d, const uint8_t* __restrict__ cls, const T* __restrict__ post, T* __restrict__ st) {
+    using L = Lattice<Q>;
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        if (cls[node] != CLS_FLUID) continue;
+        int x, y, z;
+        node_xyz(node, d, x, y, z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int64_t dn = shifted(d, x, y, z, L::cx(i), L::cy(i), L::cz(i));
+            st[i * d.plane + node] = (cls[dn] == CLS_FLUID) ? post[i * d.plane + dn] : post[L::opp(i) * d.plane + node];
+        }
+    }
+}
+
+// pull layout -> post-streaming values (0 at solid nodes)
+template <int Q, typename T>
+__global__ void k_gather(Dims d, const uint8_t* __restrict__ cls, const T* __restrict__ st, T* __restrict__ post) {
+    using L = Lattice<Q>;
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        const bool fluid = cls[node] == CLS_FLUID;
+        int x, y, z;
+        node_xyz(node, d, x, y, z);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T v = T(0);
+            if (fluid) {
+                const int64_t sn = shifted(d, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
+                v = (cls[sn] == CLS_FLUID) ? st[i * d.plane + sn] : st[L::opp(i) * d.plane + node];
+            }
+            post[i * d.plane + node] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics: per-block FP64 partial records, then one fixed-order final sum
+// ---------------------------------------------------------------------------
+enum {
+    DG_PHI = 0, DG_POP, DG_NFLUID, DG_PIN, DG_NIN, DG_POUT, DG_NOUT, DG_NIFACE, DG_NFIT,
+    DG_A = 9,      // 16 entries: normal matrix of the circle/sphere fit
+    DG_B = 25,     // 4 entries
+    DG_NAN = 29,
+    DG_MAXU2 = 30, // max entries
+    DG_APEX = 31,
+    DG_REC = 32
+};
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_MAX_BLOCKS = 1024;
+
+struct ProbeDev {
+    int kind;
+    double center[3], radius, normal[3], exclude;
+};
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rho_l, double rho_g,
+                                                               const uint8_t* __restrict__ cls,
+                                                               const T* __restrict__ Nst, const T* __restrict__ phi,
+                                                               const T* __restrict__ u, const T* __restrict__ p,
+                                                               ProbeDev pr, double* __restrict__ partial) {
+    using L = Lattice<Q>;
+    constexpr int D = L::D;
+    double acc[DG_REC];
+#pragma unroll
+    for (int k = 0; k < DG_REC; ++k) acc[k] = 0.0;
+    acc[DG_APEX] = -INFINITY;
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int n[3] = {d.nx, d.ny, d.nz};
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        if (cls[node] != CLS_FLUID) continue;
+        int x, y, z;
+        node_xyz(node, d, x, y, z);
+        const double ph = (double)phi[node];
+        acc[DG_NFLUID] += 1.0;
+        acc[DG_PHI] += ph;
+        double ps = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int64_t sn = shifted(d, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
+            ps += (double)((cls[sn] == CLS_FLUID) ? Nst[i * d.plane + sn] : Nst[L::opp(i) * d.plane + node]);
+        }
+        acc[DG_POP] += ps;
+        double u2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const double ua = (double)u[a * d.plane + node];
+            u2 += ua * ua;
+        }
+        if (u2 > acc[DG_MAXU2]) acc[DG_MAXU2] = u2;
+        if (!(u2 == u2) || !(ph == ph)) acc[DG_NAN] += 1.0;
+        const double phh = (rho_l * ph + rho_g * (1.0 - ph)) * (double)p[node];
+        if (ph > 1.0 - 1e-3) { acc[DG_PIN] += phh; acc[DG_NIN] += 1.0; }
+        if (ph < 1e-3) { acc[DG_POUT] += phh; acc[DG_NOUT] += 1.0; }
+        if (pr.kind == 0) continue;
+        const int r[3] = {x, y, z};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int64_t yn = shifted(d, x, y, z, a == 0, a == 1, a == 2);
+            if (cls[yn] != CLS_FLUID) continue;
+            const double p1 = (double)phi[yn];
+            if ((ph >= 0.5) == (p1 >= 0.5)) continue;
+            const double t = (0.5 - ph) / (p1 - ph);
+            double q[3] = {0.0, 0.0, 0.0};
+            double q2 = 0.0, h = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double v = r[k] + (k == a ? t : 0.0) - pr.center[k];
+                v -= n[k] * floor(v / n[k] + 0.5);
+                q[k] = v;
+                q2 += v * v;
+                h += v * pr.normal[k];
+            }
+            acc[DG_NIFACE] += 1.0;
+            if (h > acc[DG_APEX]) acc[DG_APEX] = h;
+            const double dist = (pr.kind == 1) ? sqrt(q2) - pr.radius : h;
+            if (dist < pr.exclude) continue;
+            double row[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int k = 0; k < D; ++k) row[k] = q[k];
+            row[D] = 1.0;
+#pragma unroll
+            for (int i = 0; i <= D; ++i) {
+#pragma unroll
+                for (int j = 0; j <= D; ++j) acc[DG_A + 4 * i + j] += row[i] * row[j];
+                acc[DG_B + i] += -q2 * row[i];
+            }
+            acc[DG_NFIT] += 1.0;
+        }
+    }
+    // block reduction in a fixed order: warp shuffles, then warps in index order
+    __shared__ double s_w[DIAG_THREADS / 32][DG_REC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < DG_REC; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            v = (k >= DG_MAXU2) ? fmax(v, w) : v + w;
+        }
+        if (lane == 0) s_w[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < DG_REC) {
+        const int k = threadIdx.x;
+        double v = s_w[0][k];
+        for (int w = 1; w < DIAG_THREADS / 32; ++w) v = (k >= DG_MAXU2) ? fmax(v, s_w[w][k]) : v + s_w[w][k];
+        partial[blockIdx.x * DG_REC + k] = v;
+    }
+}
+
+static __global__ void k_diag_final(int nblocks, const double* __restrict__ partial, double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= DG_REC) return;
+    double v = partial[k];
+    for (int b = 1; b < nblocks; ++b) v = (k >= DG_MAXU2) ? fmax(v, partial[b * DG_REC + k]) : v + partial[b * DG_REC + k];
+    out[k] = v;
+}
+
+}  // namespace lbmgpu

@@ -1,0 +1,246 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative L-infinity over fluid nodes, max|gpu - oracle| / max|oracle|):
+FP64 1e-12 and FP32 1e-4 on populations, as the target states; the same bound
+is applied to phi, u and p."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_30878_gb300 import lbm
+from paper_2605_30878_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lbm.FP64: 1e-12, lbm.FP32: 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_30878_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def rel(a, b, mask=None):
+    if mask is not None:
+        a, b = a[..., mask], b[..., mask]
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def pair(cfg, precision):
+    P = dict(cfg["params"], precision=precision)
+    g = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
+    o = oracle.Oracle(cfg["params"], cfg["solid"], cfg["ghosts"])
+    return g, o
+
+
+def compare(g, o, solid, precision, what=("N", "B", "phi", "u", "p")):
+    fluid = solid.reshape(-1) == 0
+    out = {}
+    for f in what:
+        a, b = g.read(f), o.get(f)
+        out[f] = rel(a, b, fluid)
+    tol = TOL[precision]
+    bad = {k: v for k, v in out.items() if not v <= tol}
+    assert not bad, "relative L-inf above %g: %s" % (tol, bad)
+    return out
+
+
+def small_3d(theta=60.0, rho_ratio=1000.0, shape=(28, 36, 40), R=7.0, R0=6.0):
+    nz, ny, nx = shape
+    center = (nx / 2.0 - 0.3, ny / 2.0 + 0.2, nz / 2.0 - 0.1)
+    solid, ghosts = wl.sphere_domain(19, shape, center, R)
+    params = dict(lattice=19, nx=nx, ny=ny, nz=nz, periodic=7, rho_l=rho_ratio, rho_g=1.0,
+                  mu_l=0.1 * (100.0 if rho_ratio > 1 else 1.0), mu_g=0.1, sigma=0.005, W=4.0, M_phi=0.02,
+                  theta=math.radians(theta), g=(0, 0, 0))
+    drop = wl.droplet_on_sphere_center(center, R, R0, math.radians(theta))
+    return dict(params=params, solid=solid, ghosts=ghosts, drop_center=tuple(drop), R0=R0)
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+def test_state_roundtrip(precision):
+    cfg = small_3d()
+    g = lbm.Domain(dict(cfg["params"], precision=precision), cfg["solid"], cfg["ghosts"])
+    fluid = cfg["solid"].reshape(-1) == 0
+    N, B, u, p = wl.random_state(19, fluid.size, fluid, seed=1)
+    phi = np.where(fluid, np.random.default_rng(2).uniform(0, 1, fluid.size), 0.0)
+    for f, v in (("N", N), ("B", B), ("u", u), ("p", p), ("phi", phi)):
+        g.write(f, v)
+        r = g.read(f)
+        tol = 0.0 if precision == lbm.FP64 else 1e-7
+        assert rel(r, v, fluid) <= tol
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+def test_initial_state_matches(precision):
+    cfg = wl.cylinder_config()
+    g, o = pair(cfg, precision)
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    compare(g, o, cfg["solid"], precision)
+    # the ghost table is the same reading of Fig. 2 on both sides
+    gc, gw, gn = g.ghost_table()
+    oc, ow, on = o.ghost_table()
+    assert np.array_equal(gn, on)
+    for k in range(len(gn)):
+        m = gn[k]
+        assert np.array_equal(gc[k, :m], oc[k, :m])
+        assert np.abs(gw[k, :m] - ow[k, :m]).max() < 1e-15
+    assert g.ghost_fallbacks() == o.ghost_fallbacks()
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+@pytest.mark.parametrize("rho_ratio", [1.0, 1000.0])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+def test_one_step_from_a_random_state(Q, rho_ratio, precision):
+    """One step from identical seeded non-equilibrium states (every term active)."""
+    if Q == 9:
+        cfg = wl.cylinder_config(nx=48, ny=40, R=9.0, R0=7.0)
+        cfg["params"].update(rho_l=rho_ratio, mu_l=0.1 * (100 if rho_ratio > 1 else 1), mu_g=0.1,
+                             g=(1e-6, -2e-6, 0))
+    else:
+        cfg = small_3d(rho_ratio=rho_ratio)
+        cfg["params"]["g"] = (1e-6, 0, -2e-6)
+    g, o = pair(cfg, precision)
+    fluid = cfg["solid"].reshape(-1) == 0
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    chi = o.get("N")[:, np.nonzero(fluid)[0][0]]
+    N, B, u, p = wl.random_state(Q, fluid.size, fluid, seed=7, base=chi)
+    phi0 = o.get("phi")
+    B = N * np.where(fluid, phi0, 0.0)[None, :] + 1e-4 * (B - N * 0.5)
+    phi = np.where(fluid, B.sum(0), phi0)
+    for obj in (g, o):
+        setter = obj.write if obj is g else obj.set
+        setter("N", N); setter("B", B); setter("u", u); setter("p", p); setter("phi", phi)
+    g.step(1)
+    o.step(1)
+    compare(g, o, cfg["solid"], precision)
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+def test_cylinder_64_parity_over_2000_steps(precision):
+    """D2Q9 64x64, cylinder R = 12, drop R0 = 10 tangent on top, theta = 60 deg,
+    density ratio 1, tau = 1: GPU vs oracle after 1, 10, 100 and 2000 steps."""
+    cfg = wl.cylinder_config()
+    g, o = pair(cfg, precision)
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    done = 0
+    for target in (1, 10, 100, 2000):
+        g.step(target - done)
+        o.step(target - done)
+        done = target
+        compare(g, o, cfg["solid"], precision)
+    probe_o = oracle.make_probe(1, cfg["solid_center"], cfg["R"], (0, 1, 0), 6.0)
+    probe_g = lbm.make_probe(1, cfg["solid_center"], cfg["R"], (0, 1, 0), 6.0)
+    dg, do = g.diagnostics(probe_g), o.diagnostics(probe_o)
+    tol = 1e-10 if precision == lbm.FP64 else 1e-4
+    for k in ("phi_sum", "pop_sum", "mass_liquid", "mass_gas", "fit_radius", "apex", "p_in", "p_out"):
+        assert abs(dg[k] - do[k]) <= tol * max(1.0, abs(do[k])), k
+    assert abs(dg["max_u"] - do["max_u"]) <= tol * 10 * do["max_u"] + 1e-15
+    assert dg["n_fluid"] == do["n_fluid"] and dg["n_iface"] == do["n_iface"]
+    assert abs(math.degrees(dg["contact_angle"] - do["contact_angle"])) < (1e-6 if precision == lbm.FP64 else 0.5)
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+def test_sphere_3d_parity_ragged_tiles(precision):
+    """D3Q19 40x36x28 (ragged against the 32x4x2 tiles), sphere R = 7, drop on its
+    pole at theta = 60 deg, density ratio 1000, viscosity ratio 100."""
+    cfg = small_3d()
+    g, o = pair(cfg, precision)
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    done = 0
+    for target in (1, 10, 40):
+        g.step(target - done)
+        o.step(target - done)
+        done = target
+        compare(g, o, cfg["solid"], precision)
+
+
+@pytest.mark.parametrize("shape,Q", [((1, 3, 5), 9), ((3, 2, 5), 19), ((1, 1, 1), 9), ((2, 2, 2), 19)])
+def test_tiny_and_solid_free_domains(shape, Q):
+    nz, ny, nx = shape
+    solid = np.zeros(shape, np.uint8)
+    params = dict(lattice=Q, nx=nx, ny=ny, nz=nz, periodic=7, rho_l=10.0, rho_g=1.0, mu_l=1.0, mu_g=0.1,
+                  sigma=0.01, W=4.0, M_phi=0.02, theta=math.radians(45), g=(1e-5, 0, 0))
+    empty = (np.zeros(0, np.int64), np.zeros((0, 3)))
+    cfg = dict(params=params, solid=solid, ghosts=empty)
+    g, o = pair(cfg, lbm.FP64)
+    rng = np.random.default_rng(5)
+    phi = rng.uniform(0, 1, nx * ny * nz)
+    g.init_phi(phi)
+    o.init_phi(phi)
+    g.step(3)
+    o.step(3)
+    compare(g, o, solid, lbm.FP64)
+    assert g.launches_per_step() == 2
+
+
+def test_neutral_angle_and_flat_wall_fp64():
+    """theta = 90 deg (eps = 0, phi_G = phi_F) on flat walls in a non-periodic channel."""
+    shape = (1, 24, 40)
+    solid, ghosts = wl.wall_domain(9, shape, 1, 1)
+    params = dict(lattice=9, nx=40, ny=24, nz=1, periodic=1, rho_l=1.0, rho_g=1.0, mu_l=1 / 6, mu_g=1 / 6,
+                  sigma=0.01, W=4.0, M_phi=0.02, theta=math.pi / 2, g=(0, 0, 0))
+    cfg = dict(params=params, solid=solid, ghosts=ghosts)
+    g, o = pair(cfg, lbm.FP64)
+    g.init_droplet((20, 1, 0), 9)
+    o.init_droplet((20, 1, 0), 9)
+    g.step(50)
+    o.step(50)
+    compare(g, o, solid, lbm.FP64)
+
+
+def test_mass_conservation_and_determinism_fp64():
+    cfg = small_3d(rho_ratio=10.0)
+    P = dict(cfg["params"], precision=lbm.FP64)
+    runs = []
+    for _ in range(2):
+        g = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
+        g.init_droplet(cfg["drop_center"], cfg["R0"])
+        d0 = g.diagnostics()
+        g.step(300)
+        d1 = g.diagnostics()
+        assert abs(d1["phi_sum"] - d0["phi_sum"]) < 1e-12 * d0["phi_sum"] * 10
+        assert abs(d1["pop_sum"] - d1["n_fluid"]) < 1e-12 * d1["n_fluid"]
+        runs.append((g.read("N"), g.read("B")))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+def test_instability_is_reported_not_faulted():
+    """A blow-up (sigma far beyond stability) surfaces as LBM_ERR_UNSTABLE at the
+    next synchronising call; the context stays usable."""
+    cfg = wl.cylinder_config()
+    P = dict(cfg["params"], precision=lbm.FP32, sigma=50.0)
+    g = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    g.step(400)
+    with pytest.raises(lbm.LbmError) as e:
+        g.sync()
+    assert e.value.status == lbm.LBM_ERR_UNSTABLE
+    g.init_droplet(cfg["drop_center"], cfg["R0"])     # re-initialising clears the flag
+    g.sync()
+
+
+def test_step_arguments():
+    cfg = wl.cylinder_config()
+    g = lbm.Domain(dict(cfg["params"], precision=lbm.FP32), cfg["solid"], cfg["ghosts"])
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    g.step(0)
+    with pytest.raises(lbm.LbmError) as e:
+        g.step(-1)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    a = lbm.Domain(dict(cfg["params"], precision=lbm.FP64), cfg["solid"], cfg["ghosts"], workspace="library")
+    b = lbm.Domain(dict(cfg["params"], precision=lbm.FP64), cfg["solid"], cfg["ghosts"], workspace="torch")
+    for d in (a, b):
+        d.init_droplet(cfg["drop_center"], cfg["R0"])
+        d.step(13)       # odd count: exercises both single-step graphs and the 8-step graph
+    assert np.array_equal(a.read("B"), b.read("B"))
