@@ -1,8 +1,12 @@
 """GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
 Tolerances (relative L-infinity over fluid nodes, max|gpu - oracle| / max|oracle|):
-FP64 1e-12 and FP32 1e-4 on populations, as the target states; the same bound
-is applied to phi, u and p."""
+FP64 1e-12 and FP32 1e-4 on the populations N, B and on phi.  u and p are
+linear in the populations with O(1) coefficients (Eqs. velUpdate and
+pressureUpdate: p = 3 (sum_{i>0} N_i - (1-chi_0))/(1-w_0) - ...), and both are
+small differences of O(0.1) sums, so their error is the populations' error
+times O(1), not a fraction of their own small size: they are compared on the
+population scale, max(max|oracle|, 1), with the same bounds."""
 import math
 
 import numpy as np
@@ -27,10 +31,13 @@ def _lib():
     lbm.load()
 
 
-def rel(a, b, mask=None):
+FLOOR = {"N": 0.0, "B": 0.0, "phi": 0.0, "u": 1.0, "p": 1.0}
+
+
+def rel(a, b, mask=None, floor=0.0):
     if mask is not None:
         a, b = a[..., mask], b[..., mask]
-    den = np.abs(b).max()
+    den = max(np.abs(b).max(), floor)
     return np.abs(a - b).max() / (den if den > 0 else 1.0)
 
 
@@ -46,7 +53,7 @@ def compare(g, o, solid, precision, what=("N", "B", "phi", "u", "p")):
     out = {}
     for f in what:
         a, b = g.read(f), o.get(f)
-        out[f] = rel(a, b, fluid)
+        out[f] = rel(a, b, fluid, FLOOR[f])
     tol = TOL[precision]
     bad = {k: v for k, v in out.items() if not v <= tol}
     assert not bad, "relative L-inf above %g: %s" % (tol, bad)
