@@ -193,6 +193,34 @@ int32_t lbm_launches_per_step(const lbm_domain* dom);
 double  lbm_bytes_per_fluid_node(const lbm_domain* dom);
 int64_t lbm_fluid_nodes(const lbm_domain* dom);
 
+/* Per-phase sums of a color field that already sits in the caller's device
+ * memory, for callers that cannot allocate device memory when they need them
+ * (a program whose device memory all belongs to its own pool allocator, a
+ * real-time loop that forbids allocation after start-up, a plugin whose host
+ * reserves every allocation).  The paper has no counterpart: this is a
+ * service of this library, not a step of the method.
+ *   dev_class  uint8[n_nodes] node classes, 0 = fluid (others are skipped)
+ *   dev_phi    T[n_nodes] color, T = float (LBM_FP32) or double (LBM_FP64)
+ *   dev_u      T[n_components][plane] velocity components (may be NULL if
+ *              n_components = 0), plane >= n_nodes
+ *   dev_out    double[6], written: fluid node count, sum phi, rho_l sum phi,
+ *              rho_g sum (1-phi), max |u|, count of non-finite phi or u
+ * Everything is device memory owned by the caller; the call only enqueues two
+ * kernels on cuda_stream (NULL = default stream) and returns.  It allocates
+ * nothing: its scratch is a static 64 KiB array inside the library that each
+ * GPU loading the library keeps until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call outside any stream capture.  All calls on a
+ * GPU share the array, so calls whose kernels overlap on the GPU (different
+ * streams, no ordering between them) race and give wrong sums; calls on one
+ * stream are safe.  n_nodes above 16,777,216 (the array's capacity of 1024
+ * blocks x 16384 nodes) is rejected with LBM_ERR_ARG.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_CUDA; a message goes to err[err_len] when err is not NULL. */
+lbm_status lbm_phase_sums_noalloc(const uint8_t* dev_class, const void* dev_phi, const void* dev_u,
+                                  int32_t precision, int32_t n_components, int64_t n_nodes,
+                                  int64_t plane, double rho_l, double rho_g, double* dev_out,
+                                  void* cuda_stream, char* err, size_t err_len);
+
 /* Message of the last failed call on dom, or of the last failed
  * lbm_create_domain when dom is NULL. */
 const char* lbm_last_error(const lbm_domain* dom);

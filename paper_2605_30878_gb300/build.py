@@ -1,6 +1,6 @@
 """Compile the CUDA library (csrc/*.cu) for sm_103a into _build/liblbm.so.
 
-Three translation units compile in parallel with nvcc and link into one
+The translation units compile in parallel with nvcc and link into one
 shared library with the CUDA runtime linked statically; the Python binding
 loads it with ctypes.
 """
@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_kern_f32.cu", "lbm_kern_f64.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kern_f32.cu", "lbm_kern_f64.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + CSRC, "-I" + os.path.join(ROOT, "include")]

@@ -23,7 +23,8 @@ FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 # Every entry point include/lbm.h declares.
 EXPORTS = ("lbm_domain_bytes", "lbm_create_domain", "lbm_init_droplet", "lbm_init_phi", "lbm_step", "lbm_sync",
            "lbm_diagnostics", "lbm_read_state", "lbm_write_state", "lbm_profile_steps", "lbm_ghost_table", "lbm_ghost_fallbacks",
-           "lbm_launches_per_step", "lbm_bytes_per_fluid_node", "lbm_fluid_nodes", "lbm_last_error", "lbm_destroy")
+           "lbm_launches_per_step", "lbm_bytes_per_fluid_node", "lbm_fluid_nodes", "lbm_last_error", "lbm_destroy",
+           "lbm_phase_sums_noalloc")
 
 
 class LbmError(RuntimeError):
@@ -106,6 +107,10 @@ def load():
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_destroy.argtypes = [C.c_void_p]
     L.lbm_destroy.restype = None
+    L.lbm_phase_sums_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64,
+                                         C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_char_p,
+                                         C.c_size_t]
+    L.lbm_phase_sums_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -147,6 +152,18 @@ def last_error(handle=None):
 def _check(status, handle=None):
     if status != LBM_OK:
         raise LbmError(status, last_error(handle))
+
+
+def phase_sums_noalloc(dev_class, dev_phi, dev_u, precision, n_components, n_nodes, plane, rho_l, rho_g,
+                       dev_out, stream=None):
+    """Per-phase sums of caller-owned device buffers (raw device addresses as
+    ints), written to dev_out (6 doubles) without any device allocation; see
+    lbm_phase_sums_noalloc in include/lbm.h.  Raises LbmError on a bad status."""
+    err = C.create_string_buffer(256)
+    st = load().lbm_phase_sums_noalloc(dev_class, dev_phi, dev_u, int(precision), int(n_components), int(n_nodes),
+                                       int(plane), float(rho_l), float(rho_g), dev_out, stream, err, 256)
+    if st != LBM_OK:
+        raise LbmError(st, err.value.decode())
 
 
 def ghost_array(nodes, normals):
