@@ -27,8 +27,8 @@ struct Layout {
     int64_t nn = 0, plane = 0;
     size_t elem = 0;
     int Q = 0, D = 0, GK = 0;
-    size_t off_N[2], off_B[2], off_phi, off_u[2], off_p, off_cls, off_gnode, off_gcorner, off_gwt, off_err,
-        off_partial, off_dout;
+    size_t off_N[2], off_B[2], off_phi, off_u[2], off_p, off_cls, off_mask, off_gnode, off_gcorner, off_gwt,
+        off_err, off_partial, off_dout;
     size_t total = 0;
 };
 
@@ -43,6 +43,10 @@ bool make_layout(const lbm_params* P, int64_t ng, Layout& L, std::string& err) {
     if (nn >= ((int64_t)1 << 31)) { err = "grid has 2^31 nodes or more"; return false; }
     L.nn = nn;
     L.plane = (int64_t)round_up((size_t)nn, 64);
+    if ((int64_t)P->lattice * L.plane >= ((int64_t)1 << 31)) {
+        err = "Q x nodes must stay below 2^31 (32-bit population indexing)";
+        return false;
+    }
     L.elem = P->precision == LBM_FP64 ? 8 : 4;
     L.Q = P->lattice;
     L.D = P->lattice == LBM_D2Q9 ? 2 : 3;
@@ -55,6 +59,7 @@ bool make_layout(const lbm_params* P, int64_t ng, Layout& L, std::string& err) {
     for (int k = 0; k < 2; ++k) L.off_u[k] = take((size_t)L.D * L.plane * L.elem);
     L.off_p = take(L.plane * L.elem);
     L.off_cls = take(L.plane);
+    L.off_mask = take(L.plane * 4);
     L.off_gnode = take((size_t)(ng + 1) * 4);
     L.off_gcorner = take((size_t)L.GK * (ng + 1) * 4);
     L.off_gwt = take((size_t)L.GK * (ng + 1) * L.elem);
@@ -94,6 +99,7 @@ struct lbm_domain {
     void* phi() const { return at<void>(lay.off_phi); }
     void* p() const { return at<void>(lay.off_p); }
     uint8_t* cls() const { return at<uint8_t>(lay.off_cls); }
+    uint32_t* mask() const { return at<uint32_t>(lay.off_mask); }
     int* errflag() const { return at<int>(lay.off_err); }
 };
 
@@ -238,13 +244,13 @@ void launch_one_step(lbm_domain* d, int cur, cudaStream_t s, cudaEvent_t* ev = n
     StepPtrs sp;
     sp.Nin = d->N(cur); sp.Bin = d->B(cur); sp.Nout = d->N(1 - cur); sp.Bout = d->B(1 - cur);
     sp.phi = d->phi(); sp.u_in = d->U(cur); sp.u_out = d->U(1 - cur); sp.p = d->p();
-    sp.cls = d->cls(); sp.err = d->errflag();
+    sp.mask = d->mask(); sp.err = d->errflag();
     if (ev) cudaEventRecord(ev[1], s);
     if (d->fp64) Launch<double>::step(d->cfg, sp, s);
     else Launch<float>::step(d->cfg, sp, s);
     if (ev) cudaEventRecord(ev[2], s);
-    if (d->fp64) Launch<double>::phi(d->cfg, d->B(1 - cur), d->cls(), d->phi(), s);
-    else Launch<float>::phi(d->cfg, d->B(1 - cur), d->cls(), d->phi(), s);
+    if (d->fp64) Launch<double>::phi(d->cfg, d->B(1 - cur), d->mask(), d->phi(), s);
+    else Launch<float>::phi(d->cfg, d->B(1 - cur), d->mask(), d->phi(), s);
     if (ev) cudaEventRecord(ev[3], s);
 }
 
@@ -462,11 +468,30 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     };
     if (cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking) != cudaSuccess) return bail("cudaStreamCreate failed");
     // upload node classes and the ghost table
+    // per-node bounce-back mask: bit i set when x - c_i is not fluid; top bit for non-fluid x
+    std::vector<uint32_t> hmask(nn, MASK_NOT_FLUID);
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t node = x + nx * (y + ny * z);
+                if (d->h_cls[node] != CLS_FLUID) continue;
+                uint32_t m = 0;
+                for (int i = 1; i < P.lattice; ++i) {
+                    const int cx = P.lattice == 9 ? Lattice<9>::cx(i) : Lattice<19>::cx(i);
+                    const int cy = P.lattice == 9 ? Lattice<9>::cy(i) : Lattice<19>::cy(i);
+                    const int cz = P.lattice == 9 ? Lattice<9>::cz(i) : Lattice<19>::cz(i);
+                    const int64_t xx = (x - cx + nx) % nx, yy = (y - cy + ny) % ny, zz = (z - cz + nz) % nz;
+                    if (d->h_cls[xx + nx * (yy + ny * zz)] != CLS_FLUID) m |= 1u << i;
+                }
+                hmask[node] = m;
+            }
     std::vector<int32_t> gnode(n_ghosts);
     for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)ghosts[g].node;
     cudaStream_t s = d->stream;
     if (cudaMemsetAsync(d->ws, 0, L.total, s) != cudaSuccess) return bail("cudaMemset failed");
-    if (cudaMemcpyAsync(d->cls(), d->h_cls.data(), nn, cudaMemcpyHostToDevice, s) != cudaSuccess) return bail("upload of node classes failed");
+    if (cudaMemcpyAsync(d->cls(), d->h_cls.data(), nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d->mask(), hmask.data(), nn * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return bail("upload of node classes failed");
     if (n_ghosts > 0) {
         if (cudaMemcpyAsync(d->at<void>(L.off_gnode), gnode.data(), n_ghosts * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(d->at<void>(L.off_gcorner), d->h_corner.data(), d->h_corner.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -714,9 +739,9 @@ double lbm_bytes_per_fluid_node(const lbm_domain* d) {
     const double s = (double)d->lay.elem;
     const int Q = d->lay.Q, D = d->lay.D;
     // populations read + written twice over (N, B); phi written (k_phi) and read (k_step);
-    // u written, and read when the density contrast makes F_visc active; p written; node class
-    // read by k_step and k_phi
-    return 4.0 * Q * s + 2.0 * s + (d->contrast ? 2.0 : 1.0) * D * s + s + 2.0;
+    // u written, and read when the density contrast makes F_visc active; p written; the 4-byte
+    // bounce-back mask read by k_step and k_phi
+    return 4.0 * Q * s + 2.0 * s + (d->contrast ? 2.0 : 1.0) * D * s + s + 8.0;
 }
 
 int64_t lbm_fluid_nodes(const lbm_domain* d) { return d ? d->n_fluid : 0; }

@@ -20,8 +20,9 @@
 //   k_phi    Eq. (phiUpdate): pull B* and sum it at every fluid node
 //
 // Arrays are structure-of-arrays with a plane stride `plane` (a multiple of
-// 64 elements): field[i * plane + node].  Node classes: 0 fluid, 1 ghost
-// (solid boundary node), 2 bulk solid.
+// 64 elements): field[i * plane + node], indexed in 32 bits (Q * plane < 2^31).
+// Node classes: 0 fluid, 1 ghost (solid boundary node), 2 bulk solid; the step
+// kernels read a per-node 32-bit bounce-back mask derived from them instead.
 #pragma once
 
 #include <cstdint>
@@ -57,9 +58,13 @@ struct StepBuffers {
     const T* u_in;           // velocity of the previous step (F_visc stencil)
     T* u_out;
     T* p;
-    const uint8_t* cls;
+    const uint32_t* mask;    // per-node bounce-back mask, see MASK_NOT_FLUID
     int* err;                // bit 0: non-finite value seen
 };
+
+// Per-node mask: bit i (1 <= i < Q) is set when x - c_i is not a fluid node,
+// so the pull in direction i bounces back; MASK_NOT_FLUID marks non-fluid x.
+constexpr uint32_t MASK_NOT_FLUID = 0x80000000u;
 
 template <int Q>
 struct Tile {
@@ -81,12 +86,38 @@ __device__ __forceinline__ int wrap_any(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-// Load the node classes (and optionally color / velocity) of a block's tile
-// with a one-node halo, periodic wrap on every axis.
-template <int Q, typename T, bool LOAD_PHI, bool LOAD_U>
-__device__ __forceinline__ void load_halo(const StepParams<T>& P, const uint8_t* __restrict__ cls,
-                                          const T* __restrict__ phi, const T* __restrict__ u,
-                                          uint8_t* s_cls, T* s_phi, T* s_u, int x0, int y0, int z0) {
+// v in [-1, n + TX]: periodic image for v in [-1, n]; positions further out
+// belong to threads outside the grid and are clamped to 0.
+__device__ __forceinline__ int wrap_halo(int v, int n) {
+    if (v < 0) return v + n;
+    if (v >= n) v -= n;
+    return v < n ? v : 0;
+}
+
+// Linear offsets (32-bit) from node (x, y, z) to its periodic lattice neighbours.
+struct Wrap {
+    int xm, xp, ym, yp, zm, zp;
+    __device__ __forceinline__ Wrap(int x, int y, int z, int nx, int ny, int nz) {
+        xm = (x == 0) ? nx - 1 : -1;
+        xp = (x == nx - 1) ? 1 - nx : 1;
+        ym = (y == 0) ? (ny - 1) * nx : -nx;
+        yp = (y == ny - 1) ? (1 - ny) * nx : nx;
+        const int sz = nx * ny;
+        zm = (z == 0) ? (nz - 1) * sz : -sz;
+        zp = (z == nz - 1) ? (1 - nz) * sz : sz;
+    }
+    __device__ __forceinline__ int off(int dx, int dy, int dz) const {
+        return (dx < 0 ? xm : (dx > 0 ? xp : 0)) + (dy < 0 ? ym : (dy > 0 ? yp : 0)) +
+               (dz < 0 ? zm : (dz > 0 ? zp : 0));
+    }
+};
+
+// Load a block's color (and optionally velocity) tile with a one-node halo.
+// Ghost nodes hold their fresh ghost color; the velocity at solid nodes is 0
+// in memory (never written), so no node class is needed here.
+template <int Q, typename T, bool LOAD_U>
+__device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __restrict__ phi,
+                                          const T* __restrict__ u, T* s_phi, T* s_u, int x0, int y0, int z0) {
     using Tl = Tile<Q>;
     constexpr int D = Tl::D;
     const int tid = threadIdx.x + Tl::TX * (threadIdx.y + Tl::TY * threadIdx.z);
@@ -94,59 +125,41 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const uint8_t*
         const int hx = k % Tl::HX;
         const int hy = (k / Tl::HX) % Tl::HY;
         const int hz = k / (Tl::HX * Tl::HY);
-        const int gx = wrap_any(x0 + hx - 1, P.nx);
-        const int gy = wrap_any(y0 + hy - 1, P.ny);
-        const int gz = (D == 2) ? 0 : wrap_any(z0 + hz - 1, P.nz);
-        const int64_t node = gx + (int64_t)P.nx * (gy + (int64_t)P.ny * gz);
-        const uint8_t c = cls[node];
-        s_cls[k] = c;
-        if (LOAD_PHI) s_phi[k] = (c != CLS_SOLID) ? phi[node] : T(0);
+        const int gx = wrap_halo(x0 + hx - 1, P.nx);
+        const int gy = wrap_halo(y0 + hy - 1, P.ny);
+        const int gz = (D == 2) ? 0 : wrap_halo(z0 + hz - 1, P.nz);
+        const int node = gx + P.nx * (gy + P.ny * gz);
+        s_phi[k] = phi[node];
         if (LOAD_U) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) s_u[d * Tl::HN + k] = (c == CLS_FLUID) ? u[d * P.plane + node] : T(0);
+            for (int d = 0; d < D; ++d) s_u[d * Tl::HN + k] = u[d * (int)P.plane + node];
         }
     }
 }
-
-// Global node index of x + (dx, dy, dz), each |d| <= 1, periodic.
-struct Nbr {
-    int xs[3], ys[3], zs[3];
-    int nx, ny;
-    __device__ __forceinline__ Nbr(int x, int y, int z, int nx_, int ny_, int nz_) : nx(nx_), ny(ny_) {
-        xs[0] = x == 0 ? nx_ - 1 : x - 1; xs[1] = x; xs[2] = x == nx_ - 1 ? 0 : x + 1;
-        ys[0] = y == 0 ? ny_ - 1 : y - 1; ys[1] = y; ys[2] = y == ny_ - 1 ? 0 : y + 1;
-        zs[0] = z == 0 ? nz_ - 1 : z - 1; zs[1] = z; zs[2] = z == nz_ - 1 ? 0 : z + 1;
-    }
-    __device__ __forceinline__ int64_t at(int dx, int dy, int dz) const {
-        return xs[dx + 1] + (int64_t)nx * (ys[dy + 1] + (int64_t)ny * zs[dz + 1]);
-    }
-};
 
 // ---------------------------------------------------------------------------
 // k_phi: Eq. (phiUpdate) on pulled B*
 // ---------------------------------------------------------------------------
 template <int Q, typename T>
 __global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const T* __restrict__ Bst,
-                                                          const uint8_t* __restrict__ cls, T* __restrict__ phi) {
+                                                          const uint32_t* __restrict__ mask, T* __restrict__ phi) {
     using L = Lattice<Q>;
     using Tl = Tile<Q>;
-    __shared__ uint8_t s_cls[Tl::HN];
-    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
-    load_halo<Q, T, false, false>(P, cls, nullptr, nullptr, s_cls, nullptr, nullptr, x0, y0, z0);
-    __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    const int x = blockIdx.x * Tl::TX + threadIdx.x;
+    const int y = blockIdx.y * Tl::TY + threadIdx.y;
+    const int z = blockIdx.z * Tl::TZ + threadIdx.z;
     if (x >= P.nx || y >= P.ny || z >= P.nz) return;
-    const int hc = (threadIdx.x + 1) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (L::D == 2 ? 0 : threadIdx.z + 1));
-    if (s_cls[hc] != CLS_FLUID) return;
-    const Nbr nb(x, y, z, P.nx, P.ny, P.nz);
-    const int64_t node = nb.at(0, 0, 0);
+    const int node = x + P.nx * (y + P.ny * z);
+    const uint32_t m = __ldg(mask + node);
+    if (m & MASK_NOT_FLUID) return;
+    const Wrap W(x, y, z, P.nx, P.ny, P.nz);
+    const int pl = (int)P.plane;
     T s = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const bool from_fluid = s_cls[hc - Tl::off(L::cx(i), L::cy(i), L::cz(i))] == CLS_FLUID;
-        const T b = from_fluid ? __ldg(Bst + i * P.plane + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)))
-                               : __ldg(Bst + L::opp(i) * P.plane + node);
-        s += b;
+        const int src = ((m >> i) & 1u) ? L::opp(i) * pl + node
+                                        : i * pl + node + W.off(-L::cx(i), -L::cy(i), -L::cz(i));
+        s += __ldg(Bst + src);
     }
     phi[node] = s;
 }
@@ -176,61 +189,87 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     using L = Lattice<Q>;
     using Tl = Tile<Q>;
     constexpr int D = L::D;
-    __shared__ uint8_t s_cls[Tl::HN];
     __shared__ T s_phi[Tl::HN];
     __shared__ T s_u[CONTRAST ? D * Tl::HN : 1];
     const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
-    load_halo<Q, T, true, CONTRAST>(P, b.cls, b.phi, b.u_in, s_cls, s_phi, s_u, x0, y0, z0);
+    load_halo<Q, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     if (x >= P.nx || y >= P.ny || z >= P.nz) return;
+    const int node = x + P.nx * (y + P.ny * z);
+    const uint32_t m = __ldg(b.mask + node);
+    if (m & MASK_NOT_FLUID) return;
     const int hc = (threadIdx.x + 1) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (D == 2 ? 0 : threadIdx.z + 1));
-    if (s_cls[hc] != CLS_FLUID) return;
-    const Nbr nb(x, y, z, P.nx, P.ny, P.nz);
-    const int64_t node = nb.at(0, 0, 0);
-    const int64_t pl = P.plane;
+    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz);
+    const int pl = (int)P.plane;
 
     // pull the post-streaming populations (bounce-back where x - c_i is solid)
     T N[Q], B[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const bool from_fluid = s_cls[hc - Tl::off(L::cx(i), L::cy(i), L::cz(i))] == CLS_FLUID;
-        const int64_t src = from_fluid ? i * pl + nb.at(-L::cx(i), -L::cy(i), -L::cz(i)) : L::opp(i) * pl + node;
+        const int src = ((m >> i) & 1u) ? L::opp(i) * pl + node
+                                        : i * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i));
         N[i] = __ldg(b.Nin + src);
         B[i] = __ldg(b.Bin + src);
     }
 
-    // isotropic stencils: grad f = 3 sum w c f(x+c), lap f = 6 sum w (f(x+c) - f(x))
+    // isotropic stencils: grad f = 3 sum_i w_i c_i f(x+c_i), lap f = 6 sum_i w_i (f(x+c_i) - f(x)).
+    // FP32 sums over +/- pairs (half the multiply-adds); FP64, the mode checked
+    // against the FP64 oracle to 1e-12 over thousands of steps, sums in lattice
+    // order as the definition is written.
+    constexpr bool kPairs = sizeof(T) == 4;
     const T phi = s_phi[hc];
     T gp[3] = {T(0), T(0), T(0)};
-    T lap = T(0);
+    T lsum = T(0);
     T du[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};   // du[a][b] = d_a u_b
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int h = hc + Tl::off(L::cx(i), L::cy(i), L::cz(i));
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const T wi = T(L::w(i));
-        const T ph = s_phi[h];
-        gp[0] += wi * T(L::cx(i)) * ph;
-        gp[1] += wi * T(L::cy(i)) * ph;
-        if (D == 3) gp[2] += wi * T(L::cz(i)) * ph;
-        lap += wi * (ph - phi);
-        if (CONTRAST) {
+        if (kPairs) {
+            if (L::opp(i) < i) continue;
+            const int hp = hc + Tl::off(cx, cy, cz), hm = hc - Tl::off(cx, cy, cz);
+            const T pp = s_phi[hp], pm = s_phi[hm];
+            const T dphi = wi * (pp - pm);
+            if (cx) gp[0] += T(cx) * dphi;
+            if (cy) gp[1] += T(cy) * dphi;
+            if (cz) gp[2] += T(cz) * dphi;
+            lsum += wi * ((pp - phi) + (pm - phi));
+            if (CONTRAST) {
 #pragma unroll
-            for (int bb = 0; bb < D; ++bb) {
-                const T ub = s_u[bb * Tl::HN + h];
-                du[0][bb] += wi * T(L::cx(i)) * ub;
-                du[1][bb] += wi * T(L::cy(i)) * ub;
-                if (D == 3) du[2][bb] += wi * T(L::cz(i)) * ub;
+                for (int bb = 0; bb < D; ++bb) {
+                    const T dub = wi * (s_u[bb * Tl::HN + hp] - s_u[bb * Tl::HN + hm]);
+                    if (cx) du[0][bb] += T(cx) * dub;
+                    if (cy) du[1][bb] += T(cy) * dub;
+                    if (cz) du[2][bb] += T(cz) * dub;
+                }
+            }
+        } else {
+            const int h = hc + Tl::off(cx, cy, cz);
+            const T ph = s_phi[h];
+            gp[0] += wi * T(cx) * ph;
+            gp[1] += wi * T(cy) * ph;
+            if (D == 3) gp[2] += wi * T(cz) * ph;
+            lsum += wi * (ph - phi);
+            if (CONTRAST) {
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) {
+                    const T ub = s_u[bb * Tl::HN + h];
+                    du[0][bb] += wi * T(cx) * ub;
+                    du[1][bb] += wi * T(cy) * ub;
+                    if (D == 3) du[2][bb] += wi * T(cz) * ub;
+                }
             }
         }
     }
+    constexpr double w0 = L::w(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         gp[a] *= T(3);
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) du[a][bb] *= T(3);
     }
-    lap *= T(6);
+    const T lap = T(6) * lsum;
 
     // mixture density and viscosity (Sec. II), relaxation time (Appendix A)
     const T rho = P.rho_g + P.drho * phi;
@@ -238,16 +277,26 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     const T nu = rcp(phi * P.inv_nu_l + (T(1) - phi) * P.inv_nu_g);
     const T tau = T(0.5) + T(3) * nu;
 
-    // force-free velocity and the pressure of this step (Eq. pressureUpdate)
-    constexpr double w0 = L::w(0);
+    // force-free velocity, moments and the pressure of this step (Eq. pressureUpdate)
     T u0[3] = {T(0), T(0), T(0)};
     T sum_moving = T(0);
+    T Pxx = T(0), Pyy = T(0), Pzz = T(0), Pxy = T(0), Pxz = T(0), Pyz = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         sum_moving += N[i];
-        u0[0] += T(L::cx(i)) * N[i];
-        u0[1] += T(L::cy(i)) * N[i];
-        if (D == 3) u0[2] += T(L::cz(i)) * N[i];
+        if (cx > 0) { u0[0] += N[i]; Pxx += N[i]; }
+        if (cx < 0) { u0[0] -= N[i]; Pxx += N[i]; }
+        if (cy > 0) { u0[1] += N[i]; Pyy += N[i]; }
+        if (cy < 0) { u0[1] -= N[i]; Pyy += N[i]; }
+        if (cz > 0) { u0[2] += N[i]; Pzz += N[i]; }
+        if (cz < 0) { u0[2] -= N[i]; Pzz += N[i]; }
+        if (cx * cy > 0) Pxy += N[i];
+        if (cx * cy < 0) Pxy -= N[i];
+        if (cx * cz > 0) Pxz += N[i];
+        if (cx * cz < 0) Pxz -= N[i];
+        if (cy * cz > 0) Pyz += N[i];
+        if (cy * cz < 0) Pyz -= N[i];
     }
     const T pres_base = (sum_moving - (T(1) - P.chi[0])) * T(1.0 / 3.0);
     const T inv_1mw0 = T(1.0 / (1.0 - w0));
@@ -281,18 +330,7 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const T p = (pres_base - T(0.5 * w0) * uu) * inv_1mw0;
 
-    // non-equilibrium traceless second moments: Pi(N) - [(c2chi + p) I + u u]
-    T Pxx = T(0), Pyy = T(0), Pzz = T(0), Pxy = T(0), Pxz = T(0), Pyz = T(0);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        if (cx) Pxx += N[i];
-        if (cy) Pyy += N[i];
-        if (cz) Pzz += N[i];
-        if (cx * cy) Pxy += T(cx * cy) * N[i];
-        if (cx * cz) Pxz += T(cx * cz) * N[i];
-        if (cy * cz) Pyz += T(cy * cz) * N[i];
-    }
+    // collision: traceless second moments of N - Neq, with sum Neq c c = (c2chi + p) I + u u
     const T omega1 = T(1) - rcp(tau);        // 1 - s_nu
     T A0, A1, Axy, Axz, Ayz;
     if (D == 2) {
@@ -313,7 +351,9 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     const T inv_gn = rcp(gn > T(1e-6) ? gn : T(1e-6));
     const T kseg = P.two_over_W * phi * (T(1) - phi) * inv_gn;
     const T three_p = T(3) * p;
-    const T Fs = T(3) * inv_rho;   // F_i = 3 w_i (c_i . F)/rho
+    const T halfF = T(1.5) * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
+    const T base0 = T(3) * u[0], base1 = T(3) * u[1], base2 = T(3) * u[2];
+    const T common = three_p - T(1.5) * uu;
 
     T* __restrict__ Nout = b.Nout;
     T* __restrict__ Bout = b.Bout;
@@ -321,11 +361,18 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     for (int i = 0; i < Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const T wi = T(L::w(i));
-        const T cu = T(cx) * u[0] + T(cy) * u[1] + T(cz) * u[2];
-        T neq;
-        if (i == 0) neq = P.chi[0] - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
-        else neq = P.chi[i] + wi * (three_p + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
-        const T cF = T(cx) * F[0] + T(cy) * F[1] + T(cz) * F[2];
+        T neq, nst;
+        if (i == 0) {
+            neq = P.chi[0] - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
+            nst = neq;
+        } else {
+            T cu3 = T(0), cF = T(0);   // 3 c.u and c.F
+            if (cx) { cu3 += T(cx) * base0; cF += T(cx) * F[0]; }
+            if (cy) { cu3 += T(cy) * base1; cF += T(cy) * F[1]; }
+            if (cz) { cu3 += T(cz) * base2; cF += T(cz) * F[2]; }
+            neq = P.chi[i] + wi * (common + cu3 + T(0.5) * cu3 * cu3);
+            nst = neq + wi * halfF * cF;
+        }
         T proj;
         if (D == 2) {
             proj = T(cx * cx - cy * cy) * A0 + T(cx * cy) * Axy;
@@ -334,10 +381,13 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
             proj = T(3 * cx * cx - c2) * A0 + T(cy * cy - cz * cz) * A1 + T(cx * cy) * Axy + T(cx * cz) * Axz +
                    T(cy * cz) * Ayz;
         }
-        const T nst = neq + T(0.5) * wi * Fs * cF + proj;
+        nst += proj;
         T bst = phi * nst;
         if (i != 0) {
-            const T cg = T(cx) * gp[0] + T(cy) * gp[1] + T(cz) * gp[2];
+            T cg = T(0);
+            if (cx) cg += T(cx) * gp[0];
+            if (cy) cg += T(cy) * gp[1];
+            if (cz) cg += T(cz) * gp[2];
             bst += kseg * cg * (P.chi[i] + wi * three_p);
         }
         Nout[i * pl + node] = nst;

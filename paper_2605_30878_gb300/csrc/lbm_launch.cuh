@@ -31,7 +31,7 @@ struct StepPtrs {
     const void* u_in;
     void* u_out;
     void* p;
-    const uint8_t* cls;
+    const uint32_t* mask;
     int* err;
 };
 
@@ -69,7 +69,7 @@ struct Launch {
         StepBuffers<T> b;
         b.Nin = (const T*)p.Nin; b.Bin = (const T*)p.Bin; b.Nout = (T*)p.Nout; b.Bout = (T*)p.Bout;
         b.phi = (T*)p.phi; b.u_in = (const T*)p.u_in; b.u_out = (T*)p.u_out; b.p = (T*)p.p;
-        b.cls = p.cls; b.err = p.err;
+        b.mask = p.mask; b.err = p.err;
         if (c.contrast)
             k_step<Q, T, true><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
         else
@@ -79,12 +79,12 @@ struct Launch {
         if (c.Q == 9) step_q<9>(c, p, s); else step_q<19>(c, p, s);
     }
 
-    static void phi(const StepConfig& c, const void* Bst, const uint8_t* cls, void* phi, cudaStream_t s) {
+    static void phi(const StepConfig& c, const void* Bst, const uint32_t* mask, void* phi, cudaStream_t s) {
         const StepParams<T> P = params(c);
         if (c.Q == 9)
-            k_phi<9, T><<<step_grid<9>(c.d), step_block<9>(), 0, s>>>(P, (const T*)Bst, cls, (T*)phi);
+            k_phi<9, T><<<step_grid<9>(c.d), step_block<9>(), 0, s>>>(P, (const T*)Bst, mask, (T*)phi);
         else
-            k_phi<19, T><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const T*)Bst, cls, (T*)phi);
+            k_phi<19, T><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const T*)Bst, mask, (T*)phi);
     }
 
     static void ghost(int GK, int64_t ng, const int32_t* node, const int32_t* corner, const void* wt, double exp_eps,
