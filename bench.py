@@ -128,10 +128,11 @@ def recorded_traffic(fluid_nodes):
 
 
 def k_step_bytes_per_fluid_node(Q, D, s, contrast):
-    """Algorithmic bytes of one k_step launch per fluid node: pull N and B (2Q s),
-    write N* and B* (2Q s), read phi (s), read the previous u (D s, only with a
-    density contrast), write u (D s) and p (s), read the 4-byte bounce-back mask."""
-    return 4 * Q * s + s + (D * s if contrast else 0) + D * s + s + 4
+    """Algorithmic bytes of one k_step launch per fluid node: pull N (Q s) -- the
+    collision needs B only through phi, which k_phi computed --, write N* and B*
+    (2Q s), read phi (s), read the previous u (D s, only with a density
+    contrast), write u (D s) and p (s), read the 4-byte bounce-back mask."""
+    return 3 * Q * s + s + (D * s if contrast else 0) + D * s + s + 4
 
 
 def workload(theta, precision, n=N_GRID):

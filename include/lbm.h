@@ -44,6 +44,12 @@ typedef enum {
 
 typedef enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 } lbm_lattice;
 
+/* Ghost-node color rule: the paper's Eq. (ghost-nodePrescription), or the
+ * comparison scheme of Fakhari et al., Eq. (ghostNodeFakhari), evaluated in
+ * the conjugate form 4 phi_F/(a + sqrt(a^2 - 2 eps phi_F)) - phi_F,
+ * a = 1 + eps/2, which is exact algebra and stays accurate at theta -> 90 deg. */
+typedef enum { LBM_GHOST_PRESENT = 0, LBM_GHOST_FAKHARI = 1 } lbm_ghost_rule;
+
 /* Arithmetic and storage type of the whole step. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1 } lbm_precision;
 
@@ -60,6 +66,8 @@ typedef struct {
     int32_t nx, ny, nz;     /* grid; nz = 1 for D2Q9 */
     uint32_t periodic;      /* bit0 x, bit1 y, bit2 z */
     int32_t precision;      /* lbm_precision */
+    int32_t ghost_rule;     /* lbm_ghost_rule */
+    int32_t reserved;       /* must be 0 */
     double rho_l, rho_g;    /* phase densities, > 0 */
     double mu_l, mu_g;      /* dynamic viscosities, > 0 */
     double sigma;           /* surface tension, Eq. (surfaceTensionForce) */

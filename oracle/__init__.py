@@ -17,7 +17,7 @@ FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 
 class Params(C.Structure):
     _fields_ = [("lattice", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("periodic", C.c_uint32), ("reserved", C.c_int32),
+                ("periodic", C.c_uint32), ("ghost_rule", C.c_int32),
                 ("rho_l", C.c_double), ("rho_g", C.c_double), ("mu_l", C.c_double), ("mu_g", C.c_double),
                 ("sigma", C.c_double), ("W", C.c_double), ("M_phi", C.c_double), ("theta", C.c_double),
                 ("g", C.c_double * 3)]
@@ -83,6 +83,8 @@ def lib():
                                   C.c_double, _dp]
         L.orc_ghost_rule.argtypes = [C.c_double, C.c_double]
         L.orc_ghost_rule.restype = C.c_double
+        L.orc_ghost_rule_fakhari.argtypes = [C.c_double, C.c_double]
+        L.orc_ghost_rule_fakhari.restype = C.c_double
         _lib = L
     return _lib
 
@@ -158,6 +160,10 @@ def collide(lattice, N, u, p, F, rho, tau, M_phi=0.02):
 
 def ghost_rule(phiF, eps):
     return lib().orc_ghost_rule(float(phiF), float(eps))
+
+
+def ghost_rule_fakhari(phiF, eps):
+    return lib().orc_ghost_rule_fakhari(float(phiF), float(eps))
 
 
 # ---------------------------------------------------------------- whole grid

@@ -320,6 +320,16 @@ double orc_ghost_rule(double phiF, double eps) {
     return phiF / (phiF + (1.0 - phiF) * exp(eps));
 }
 
+/* Eq. (ghostNodeFakhari), the comparison scheme.  As printed it divides a
+ * difference that vanishes with eps by eps (theta = 90 deg needs care,
+ * Sec. II); multiplying by the conjugate gives the same expression without
+ * that cancellation:  (2/eps)(a - sqrt(a^2 - 2 eps phi_F)) = 4 phi_F / (a + sqrt(...)),
+ * a = 1 + eps/2, which is phi_G = phi_F at eps = 0. */
+double orc_ghost_rule_fakhari(double phiF, double eps) {
+    double a = 1.0 + eps / 2.0;
+    return 4.0 * phiF / (a + sqrt(a * a - 2.0 * eps * phiF)) - phiF;
+}
+
 /* ------------------------------------------------------------------ */
 /* grid helpers                                                         */
 /* ------------------------------------------------------------------ */
@@ -479,7 +489,8 @@ static void update_ghosts(const orc_sim* s, const double* phi_in, double* phi_ou
     for (int64_t g = 0; g < s->ng; ++g) {
         double phiF = 0;
         for (int k = 0; k < s->g_nc[g]; ++k) phiF += s->g_wt[g * GMAX + k] * phi_in[s->g_corner[g * GMAX + k]];
-        phi_out[s->g_node[g]] = phiF / (phiF + (1.0 - phiF) * s->exp_eps);
+        phi_out[s->g_node[g]] = (s->prm.ghost_rule == 1) ? orc_ghost_rule_fakhari(phiF, s->eps)
+                                                         : phiF / (phiF + (1.0 - phiF) * s->exp_eps);
     }
 }
 
@@ -499,6 +510,7 @@ int orc_create(const orc_params* prm, const uint8_t* solid, const orc_ghost* gho
     if (prm->nx < 1 || prm->ny < 1 || prm->nz < 1) FAIL("grid sizes must be positive");
     if (prm->lattice == 9 && prm->nz != 1) FAIL("D2Q9 needs nz == 1");
     if (!(prm->W >= 4.0)) FAIL("W must be >= 4 lattice units");
+    if (prm->ghost_rule != 0 && prm->ghost_rule != 1) FAIL("ghost_rule must be 0 or 1");
     if (!(prm->rho_l > 0 && prm->rho_g > 0 && prm->mu_l > 0 && prm->mu_g > 0)) FAIL("densities and viscosities must be positive");
     if (build_lattice(&s->L, prm->lattice, prm->M_phi, 0)) FAIL("lattice construction failed");
     if (!(s->L.alpha > 0 && s->L.alpha < 1)) FAIL("M_phi gives alpha outside (0,1)");

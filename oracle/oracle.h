@@ -26,7 +26,7 @@ typedef struct {
     int32_t lattice;      /* 9 (D2Q9, Appendix A) or 19 (D3Q19, 3D extension) */
     int32_t nx, ny, nz;   /* nz = 1 for D2Q9 */
     uint32_t periodic;    /* bit0 x, bit1 y, bit2 z; a non-periodic axis needs solid end layers */
-    int32_t reserved;
+    int32_t ghost_rule;   /* 0: Eq. (ghost-nodePrescription); 1: Eq. (ghostNodeFakhari) */
     double rho_l, rho_g;  /* liquid (phi=1) and gas (phi=0) densities, Sec. II */
     double mu_l, mu_g;    /* dynamic viscosities */
     double sigma;         /* surface tension, Eq. (surfaceTensionForce) */
@@ -85,6 +85,7 @@ void   orc_macro(int lattice, double M_phi, const double* N, const double F[3], 
 void   orc_collide(int lattice, double M_phi, const double* N, const double u[3], double p,
                    const double F[3], double rho, double tau, double* Nst);
 double orc_ghost_rule(double phiF, double eps);
+double orc_ghost_rule_fakhari(double phiF, double eps);
 
 #ifdef __cplusplus
 }

@@ -235,11 +235,11 @@ void launch_one_step(lbm_domain* d, int cur, cudaStream_t s, cudaEvent_t* ev = n
     if (d->ng > 0) {
         const void* wt = d->at<void>(L.off_gwt);
         if (d->fp64)
-            Launch<double>::ghost(L.GK, d->ng, d->at<int32_t>(L.off_gnode), d->at<int32_t>(L.off_gcorner), wt,
-                                  d->cfg.exp_eps, d->phi(), s);
+            Launch<double>::ghost(L.GK, d->cfg.ghost_rule, d->ng, d->at<int32_t>(L.off_gnode),
+                                  d->at<int32_t>(L.off_gcorner), wt, d->cfg.exp_eps, d->cfg.eps, d->phi(), s);
         else
-            Launch<float>::ghost(L.GK, d->ng, d->at<int32_t>(L.off_gnode), d->at<int32_t>(L.off_gcorner), wt,
-                                 d->cfg.exp_eps, d->phi(), s);
+            Launch<float>::ghost(L.GK, d->cfg.ghost_rule, d->ng, d->at<int32_t>(L.off_gnode),
+                                 d->at<int32_t>(L.off_gcorner), wt, d->cfg.exp_eps, d->cfg.eps, d->phi(), s);
     }
     StepPtrs sp;
     sp.Nin = d->N(cur); sp.Bin = d->B(cur); sp.Nout = d->N(1 - cur); sp.Bout = d->B(1 - cur);
@@ -373,6 +373,9 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     if (!solid) return fail(nullptr, LBM_ERR_ARG, "solid mask is NULL");
     if (n_ghosts > 0 && !ghosts) return fail(nullptr, LBM_ERR_ARG, "ghost list is NULL");
     if (!(P.W >= 4.0)) return fail(nullptr, LBM_ERR_ARG, "W must be >= 4 lattice units");
+    if (P.ghost_rule != LBM_GHOST_PRESENT && P.ghost_rule != LBM_GHOST_FAKHARI)
+        return fail(nullptr, LBM_ERR_ARG, "ghost_rule must be LBM_GHOST_PRESENT or LBM_GHOST_FAKHARI");
+    if (P.reserved != 0) return fail(nullptr, LBM_ERR_ARG, "reserved field of lbm_params must be 0");
     if (!(P.rho_l > 0 && P.rho_g > 0 && P.mu_l > 0 && P.mu_g > 0))
         return fail(nullptr, LBM_ERR_ARG, "densities and viscosities must be positive");
     if (!(P.sigma >= 0)) return fail(nullptr, LBM_ERR_ARG, "sigma must be >= 0");
@@ -399,7 +402,9 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     c.sigma = P.sigma; c.W = P.W;
     for (int a = 0; a < 3; ++a) c.g[a] = (L.D == 2 && a == 2) ? 0.0 : P.g[a];
     c.c2chi = c2chi;
-    c.exp_eps = std::exp(-(4.0 / P.W) * std::cos(P.theta));
+    c.eps = -(4.0 / P.W) * std::cos(P.theta);
+    c.exp_eps = std::exp(c.eps);
+    c.ghost_rule = P.ghost_rule;
 
     // node classes: a solid node with a fluid stencil neighbour is a ghost
     const int64_t nn = L.nn;

@@ -11,7 +11,7 @@
 // One time step is three launches on one stream:
 //   k_ghost  Eq. (ghost-nodePrescription) at every ghost node, from the color
 //            of the fluid corners of x_F (weights precomputed on the host)
-//   k_step   at every fluid node: pull N, B; isotropic stencils of phi (and of
+//   k_step   at every fluid node: pull N; isotropic stencils of phi (and of
 //            the previous velocity) from a shared-memory halo tile; forces of
 //            Eqs. (surfaceTensionForce), (pressCorrection), (viscCorrection),
 //            (totalForce); u, p of Eqs. (velUpdate), (pressureUpdate);
@@ -167,16 +167,26 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const
 // ---------------------------------------------------------------------------
 // k_ghost: Eq. (ghost-nodePrescription)
 // ---------------------------------------------------------------------------
-template <int GK, typename T>
+// RULE 0: the paper's rule; RULE 1: Eq. (ghostNodeFakhari) multiplied through by
+// the conjugate, 4 phi_F / (a + sqrt(a^2 - 2 eps phi_F)) - phi_F, a = 1 + eps/2,
+// which stays accurate as eps -> 0 (theta -> 90 deg) where the printed form cancels.
+template <int GK, typename T, int RULE>
 __global__ void __launch_bounds__(256) k_ghost(int64_t n_ghosts, const int32_t* __restrict__ g_node,
                                                const int32_t* __restrict__ g_corner, const T* __restrict__ g_wt,
-                                               T exp_eps, T* __restrict__ phi) {
+                                               T exp_eps, T eps, T* __restrict__ phi) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= n_ghosts) return;
     T phiF = T(0);
 #pragma unroll
     for (int k = 0; k < GK; ++k) phiF += g_wt[k * n_ghosts + g] * phi[g_corner[k * n_ghosts + g]];
-    phi[g_node[g]] = phiF / (phiF + (T(1) - phiF) * exp_eps);
+    T phiG;
+    if (RULE == 0) {
+        phiG = phiF / (phiF + (T(1) - phiF) * exp_eps);
+    } else {
+        const T a = T(1) + T(0.5) * eps;
+        phiG = T(4) * phiF / (a + sqrt(a * a - T(2) * eps * phiF)) - phiF;
+    }
+    phi[g_node[g]] = phiG;
 }
 
 // ---------------------------------------------------------------------------
@@ -203,14 +213,14 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     const Wrap Wr(x, y, z, P.nx, P.ny, P.nz);
     const int pl = (int)P.plane;
 
-    // pull the post-streaming populations (bounce-back where x - c_i is solid)
-    T N[Q], B[Q];
+    // pull the post-streaming populations N (bounce-back where x - c_i is solid);
+    // B enters the collision only through phi = sum B, which k_phi computed
+    T N[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int src = ((m >> i) & 1u) ? L::opp(i) * pl + node
                                         : i * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i));
         N[i] = __ldg(b.Nin + src);
-        B[i] = __ldg(b.Bin + src);
     }
 
     // isotropic stencils: grad f = 3 sum_i w_i c_i f(x+c_i), lap f = 6 sum_i w_i (f(x+c_i) - f(x)).

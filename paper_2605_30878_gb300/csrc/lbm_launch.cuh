@@ -20,6 +20,8 @@ struct StepConfig {
     double chi[19];
     double c2chi;
     double exp_eps;
+    double eps;                    // -(4/W) cos(theta)
+    int ghost_rule;                // lbm_ghost_rule
 };
 
 struct StepPtrs {
@@ -87,14 +89,15 @@ struct Launch {
             k_phi<19, T><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const T*)Bst, mask, (T*)phi);
     }
 
-    static void ghost(int GK, int64_t ng, const int32_t* node, const int32_t* corner, const void* wt, double exp_eps,
-                      void* phi, cudaStream_t s) {
+    static void ghost(int GK, int rule, int64_t ng, const int32_t* node, const int32_t* corner, const void* wt,
+                      double exp_eps, double eps, void* phi, cudaStream_t s) {
         if (ng == 0) return;
         const unsigned blocks = (unsigned)((ng + 255) / 256);
-        if (GK == 4)
-            k_ghost<4, T><<<blocks, 256, 0, s>>>(ng, node, corner, (const T*)wt, (T)exp_eps, (T*)phi);
-        else
-            k_ghost<8, T><<<blocks, 256, 0, s>>>(ng, node, corner, (const T*)wt, (T)exp_eps, (T*)phi);
+        const T* w = (const T*)wt;
+        if (GK == 4 && rule == 0) k_ghost<4, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+        if (GK == 4 && rule == 1) k_ghost<4, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+        if (GK == 8 && rule == 0) k_ghost<8, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+        if (GK == 8 && rule == 1) k_ghost<8, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
     }
 
     static unsigned flat_blocks(const Dims& d) {

@@ -18,6 +18,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOU
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_UNSTABLE",
                 -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_UNSUPPORTED"}
 FP64, FP32 = 0, 1
+GHOST_PRESENT, GHOST_FAKHARI = 0, 1
 FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 
 # Every entry point include/lbm.h declares.
@@ -35,8 +36,8 @@ class LbmError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("lattice", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
-                ("periodic", C.c_uint32), ("precision", C.c_int32),
-                ("rho_l", C.c_double), ("rho_g", C.c_double), ("mu_l", C.c_double), ("mu_g", C.c_double),
+                ("periodic", C.c_uint32), ("precision", C.c_int32), ("ghost_rule", C.c_int32),
+                ("reserved", C.c_int32), ("rho_l", C.c_double), ("rho_g", C.c_double), ("mu_l", C.c_double), ("mu_g", C.c_double),
                 ("sigma", C.c_double), ("W", C.c_double), ("M_phi", C.c_double), ("theta", C.c_double),
                 ("g", C.c_double * 3)]
 

@@ -219,3 +219,93 @@ def random_state(Q, nn, fluid, seed, base=None, amp=1e-3):
     p = 1e-4 * rng.uniform(-1, 1, size=nn)
     p[~fluid] = 0
     return N, B, u, p
+
+
+# ---------------------------------------------------------------- porous medium
+
+def sphere_packing(n=256, r_min=8.0, r_max=16.0, porosity=0.45, reservoir=24, seed=1, max_iter=4000,
+                   tol=0.02):
+    """Seeded non-overlapping polydisperse sphere packing in a periodic n^3 box.
+
+    Radii ~ U(r_min, r_max); sphere count from the target solid fraction
+    (1 - porosity) of the region x >= reservoir (x < reservoir stays free, the
+    inlet reservoir).  Random sequential placement jams well below a 0.55 solid
+    fraction, so the spheres are placed at random and then pushed apart pair by
+    pair (periodic in y, z; confined to the region in x) until no two overlap by
+    more than tol.  Returns (centers [m,3], radii [m])."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    L = float(n)
+    span = L - reservoir
+    vol = span * L * L * (1.0 - porosity)
+    mean_r3 = (r_max ** 4 - r_min ** 4) / (4.0 * (r_max - r_min))
+    m = int(round(vol / (4.0 / 3.0 * math.pi * mean_r3)))
+    radii = rng.uniform(r_min, r_max, m)
+    c = np.stack([reservoir + radii + rng.uniform(0, 1, m) * (span - 2 * radii),
+                  rng.uniform(0, L, m), rng.uniform(0, L, m)], axis=1)
+    box = np.array([4.0 * L, L, L])          # x never wraps: the big box length disables x periodicity
+    for _ in range(max_iter):
+        tree = cKDTree(c, boxsize=box)
+        pairs = tree.query_pairs(2.0 * r_max, output_type="ndarray")
+        if len(pairs) == 0:
+            break
+        i, j = pairs[:, 0], pairs[:, 1]
+        d = c[j] - c[i]
+        d[:, 1:] -= L * np.round(d[:, 1:] / L)
+        dist = np.linalg.norm(d, axis=1)
+        ov = radii[i] + radii[j] - dist
+        sel = ov > 0
+        if not sel.any() or ov.max() <= tol:
+            break
+        i, j, d, dist, ov = i[sel], j[sel], d[sel], dist[sel], ov[sel]
+        u = d / np.maximum(dist, 1e-9)[:, None]
+        push = 0.5 * (ov + tol)[:, None] * u
+        delta = np.zeros_like(c)
+        np.add.at(delta, i, -push)
+        np.add.at(delta, j, push)
+        c += delta
+        c[:, 0] = np.clip(c[:, 0], reservoir + radii, L - radii)
+        c[:, 1:] %= L
+    return c, radii
+
+
+def packing_domain(centers, radii, n=256):
+    """Staircase mask (|x - c|^2 <= r^2 with periodic images in y, z) of a
+    sphere packing and its D3Q19 ghost list; each ghost takes the normal of the
+    sphere surface nearest to it."""
+    from scipy.spatial import cKDTree
+    shape = (n, n, n)
+    solid = np.zeros(shape, dtype=bool)
+    for (cx, cy, cz), r in zip(centers, radii):
+        lo = np.floor(np.array([cx, cy, cz]) - r).astype(int)
+        hi = np.ceil(np.array([cx, cy, cz]) + r).astype(int)
+        xs = np.arange(lo[0], hi[0] + 1)
+        ys = np.arange(lo[1], hi[1] + 1)
+        zs = np.arange(lo[2], hi[2] + 1)
+        dz, dy, dx = np.meshgrid(zs - cz, ys - cy, xs - cx, indexing="ij")
+        inside = dx * dx + dy * dy + dz * dz <= r * r
+        zi, yi, xi = np.meshgrid(zs % n, ys % n, xs % n, indexing="ij")
+        solid[zi[inside], yi[inside], xi[inside]] = True
+    solid = solid.astype(np.uint8)
+    tree = cKDTree(centers, boxsize=np.array([4.0 * n, n, n]))
+    radii = np.asarray(radii)
+
+    def fn(x, y, z):
+        pts = np.stack([x, y, z], axis=1)
+        k = min(8, len(radii))
+        _, idx = tree.query(pts, k=k)
+        idx = idx.reshape(len(pts), k)
+        best = np.full(len(pts), np.inf)
+        out = np.zeros((len(pts), 3))
+        for col in range(k):
+            cid = idx[:, col]
+            d = pts - centers[cid]
+            d[:, 1:] -= n * np.round(d[:, 1:] / n)
+            r = np.linalg.norm(d, axis=1)
+            gap = np.abs(r - radii[cid])
+            sel = gap < best
+            rr = np.where(r == 0, 1.0, r)
+            out[sel] = d[sel] / rr[sel, None]
+            best = np.where(sel, gap, best)
+        return out
+    return solid, ghost_list(solid, 19, fn)

@@ -251,3 +251,24 @@ def test_step_arguments():
         d.init_droplet(cfg["drop_center"], cfg["R0"])
         d.step(13)       # odd count: exercises both single-step graphs and the 8-step graph
     assert np.array_equal(a.read("B"), b.read("B"))
+
+
+@pytest.mark.parametrize("theta_deg", [30.0, 90.0])
+def test_fakhari_rule_parity_fp64(theta_deg):
+    """The comparison scheme, Eq. (ghostNodeFakhari), selected by ghost_rule = 1
+    (theta = 90 deg exercises eps ~ -6e-17, where it must reduce to phi_G = phi_F)."""
+    cfg = wl.cylinder_config(theta_deg=theta_deg)
+    cfg["params"].update(ghost_rule=1, rho_l=10.0, mu_l=1.0, mu_g=0.1)
+    g, o = pair(cfg, lbm.FP64)
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    g.step(300)
+    o.step(300)
+    compare(g, o, cfg["solid"], lbm.FP64)
+    if theta_deg == 90.0:
+        cor, wt, nc = o.ghost_table()
+        phi = g.read("phi")
+        g.step(1)                        # the step opens with the ghost update
+        ghost_nodes = cfg["ghosts"][0]
+        phiF = np.array([np.dot(wt[k, :nc[k]], phi[cor[k, :nc[k]]]) for k in range(len(ghost_nodes))])
+        assert np.abs(g.read("phi")[ghost_nodes] - phiF).max() < 1e-14

@@ -156,3 +156,53 @@ def test_ghost_list_validation():
     prm = dict(cfg["params"], W=3.0)
     with pytest.raises(ValueError):
         oracle.Oracle(prm, cfg["solid"], cfg["ghosts"])                             # W < 4
+
+
+def test_fakhari_rule_solves_its_midpoint_relation():
+    """Eq. (ghostNodeFakhari) is the root of the wetting ODE discretised at the
+    midpoint s = (phi_G + phi_F)/2: phi_F - phi_G = eps s (1 - s)."""
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        phiF, eps = rng.uniform(0, 1), rng.uniform(-1, 1)
+        g = oracle.ghost_rule_fakhari(phiF, eps)
+        s = 0.5 * (g + phiF)
+        assert abs((phiF - g) - eps * s * (1 - s)) < 1e-15
+    for eps in (-1.0, -0.3, 0.4, 1.0):
+        assert abs(oracle.ghost_rule_fakhari(0.0, eps)) < 1e-15
+        assert abs(oracle.ghost_rule_fakhari(1.0, eps) - 1.0) < 1e-14
+    for phiF in np.linspace(0, 1, 11):
+        assert oracle.ghost_rule_fakhari(phiF, 0.0) == phiF            # theta = 90 deg
+        # eps computed from theta = pi/2 is -6e-17, not 0: the rule must still return phi_F
+        eps90 = -(4.0 / 4.0) * math.cos(math.pi / 2)
+        assert abs(oracle.ghost_rule_fakhari(phiF, eps90) - phiF) < 1e-15
+    for eps in (1e-3, 1e-8, -1e-12):                                   # well conditioned near 0
+        phiF = 0.37
+        g = oracle.ghost_rule_fakhari(phiF, eps)
+        s = 0.5 * (g + phiF)
+        assert abs((phiF - g) - eps * s * (1 - s)) < 4e-16          # a few ulps of phi
+
+
+def test_oracle_rules_differ_by_the_papers_series():
+    """Eq. (differenceSeriesPrescription) between the oracle's two rules."""
+    for phiF in (0.2, 0.5, 0.8):
+        for eps in (0.02, -0.02, 0.01):
+            series = eps ** 3 / 12 * (1 - 3 * (1 - phiF) * phiF) * phiF * (1 - phiF)
+            diff = oracle.ghost_rule(phiF, eps) - oracle.ghost_rule_fakhari(phiF, eps)
+            assert abs(diff - series) < 0.05 * abs(eps) ** 3
+
+
+def test_grid_ghost_update_uses_the_selected_rule():
+    nx, ny, W, theta = 40, 16, 4.0, math.radians(40)
+    solid, ghosts = wl.wall_domain(9, (1, ny, nx), bottom=1, top=1)
+    prm = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=1, rho_l=1, rho_g=1, mu_l=1 / 6, mu_g=1 / 6,
+               sigma=0.01, W=W, M_phi=0.02, theta=theta, ghost_rule=1)
+    o = oracle.Oracle(prm, solid, ghosts)
+    _, y, x = wl.node_coords((1, ny, nx))
+    exact = _planar_profile(x, y, theta, W, nx / 2, 3.0).reshape(-1)
+    o.set("phi", np.where(solid.reshape(-1) == 0, exact, 0.0))
+    o.update_ghosts()
+    got = o.get("phi")
+    eps = -(4.0 / W) * math.cos(theta)
+    for xx in range(nx):
+        g, f = xx, xx + nx                      # ghost (x, 0) and its fluid point (x, 1)
+        assert abs(got[g] - oracle.ghost_rule_fakhari(exact[f], eps)) < 1e-15
