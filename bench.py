@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
+                    help="population storage: fp32 (the bench default) or fp16 (shifted, scaled)")
     return ap.parse_args()
 
 
@@ -127,12 +129,14 @@ def recorded_traffic(fluid_nodes):
     return rec["dram_bytes_per_fluid_node"] * fluid_nodes
 
 
-def k_step_bytes_per_fluid_node(Q, D, s, contrast):
-    """Algorithmic bytes of one k_step launch per fluid node: pull N (Q s) -- the
+def k_step_bytes_per_fluid_node(Q, D, s, contrast, pop=None):
+    """Algorithmic bytes of one k_step launch per fluid node: pull N (one population
+    array: pop = Q s, or 4 + 2 (Q - 1) with FP16 moving populations) -- the
     collision needs B only through phi, which k_phi computed --, write N* and B*
-    (2Q s), read phi (s), read the previous u (D s, only with a density
-    contrast), write u (D s) and p (s), read the 4-byte bounce-back mask."""
-    return 3 * Q * s + s + (D * s if contrast else 0) + D * s + s + 4
+    (2 pop), read phi (s), read the previous u (D s, only with a density contrast),
+    write u (D s) and p (s), read the 4-byte bounce-back mask."""
+    pop = Q * s if pop is None else pop
+    return 3 * pop + s + (D * s if contrast else 0) + D * s + s + 4
 
 
 def workload(theta, precision, n=N_GRID):
@@ -232,7 +236,8 @@ def run_ours(args):
 
     lib_build.build()
     theta = args.theta if args.theta is not None else THETA_SWEEP[rank % len(THETA_SWEEP)]
-    cfg = workload(theta, lbm.FP32, n=args.n)
+    prec = lbm.FP16 if args.storage == "fp16" else lbm.FP32
+    cfg = workload(theta, prec, n=args.n)
     P = cfg["params"]
     n = args.n
     nn = n ** 3
@@ -270,10 +275,12 @@ def run_ours(args):
     kms = dom.profile_steps(prof_steps)
     t_step = kms[1] / prof_steps * 1e-3
     s, Q, D = 4, 19, 3
-    kb = k_step_bytes_per_fluid_node(Q, D, s, True) * fluid
+    sp = 2 if prec == lbm.FP16 else 4
+    pop = 4 + 2 * (Q - 1) if prec == lbm.FP16 else Q * s
+    kb = k_step_bytes_per_fluid_node(Q, D, s, True, pop) * fluid
     achieved = kb / t_step / 1e9
     peak, peak_kind = hbm_peak()
-    traffic = recorded_traffic(fluid)
+    traffic = recorded_traffic(fluid) if prec == lbm.FP32 else None
     share = kms / kms.sum()
     launches = dom.launches_per_step()
     bytes_step = dom.bytes_per_fluid_node()
@@ -286,10 +293,10 @@ def run_ours(args):
         # contact angle after the same number of steps in FP32 and FP64 (bounded)
         n_angle = min(args.warmup + args.steps, 400)
         angle = {"set_deg": theta, "after_steps": n_angle, "max_u_fp32": diag32["max_u"]}
-        for name, prec in (("fp32_deg", lbm.FP32), ("fp64_deg", lbm.FP64)):
-            if prec == lbm.FP64 and args.no_fp64_check:
+        for name, aprec in ((args.storage + "_deg", prec), ("fp64_deg", lbm.FP64)):
+            if aprec == lbm.FP64 and args.no_fp64_check:
                 continue
-            da = lbm.Domain(dict(P, precision=prec), cfg["solid"], cfg["ghosts"])
+            da = lbm.Domain(dict(P, precision=aprec), cfg["solid"], cfg["ghosts"])
             da.init_droplet(cfg["drop_center"], cfg["R0"])
             da.step(n_angle)
             angle[name] = math.degrees(da.diagnostics(probe)["contact_angle"])
@@ -297,8 +304,8 @@ def run_ours(args):
             del da
             torch.cuda.empty_cache()
         if "fp64_deg" in angle:
-            angle["fp32_vs_fp64_deg"] = abs(angle["fp32_deg"] - angle["fp64_deg"])
-        angle["fp32_deg_after_timed_run"] = math.degrees(diag32["contact_angle"])
+            angle[args.storage + "_vs_fp64_deg"] = abs(angle[args.storage + "_deg"] - angle["fp64_deg"])
+        angle[args.storage + "_deg_after_timed_run"] = math.degrees(diag32["contact_angle"])
 
         # end to end through the C ABI from host buffers: create (host mask and ghost
         # list -> device), init, K steps, diagnostics (device -> host), destroy
@@ -322,16 +329,18 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if sp == 4 else "f32 (f16 population storage)", "data": "synthetic",
             "config": {"workload": "D3Q19 %d^3 drop on sphere: sphere R=%g at the centre, drop R0=%g on the +z pole "
-                                   "at theta=%g deg, rho_l/rho_g=1000, mu_l/mu_g=100, sigma=0.005, FP32, periodic"
-                                   % (n, R_SPHERE * n / N_GRID, R_DROP * n / N_GRID, theta),
+                                   "at theta=%g deg, rho_l/rho_g=1000, mu_l/mu_g=100, sigma=0.005, %s, periodic"
+                                   % (n, R_SPHERE * n / N_GRID, R_DROP * n / N_GRID, theta,
+                                      "FP32" if sp == 4 else "FP32 arithmetic, FP16 populations"),
                        "nodes": nn, "fluid_nodes": fluid, "ghost_nodes": ng,
                        "l2": "inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (lbm.domain_bytes(P, ng) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "k_step<19,float,contrast>", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": "k_step<19,float,%s,contrast>" % ("half" if sp == 2 else "float"),
+                         "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "bytes_per_fluid_node": k_step_bytes_per_fluid_node(Q, D, s, True),
+                         "traffic": traffic, "bytes_per_fluid_node": k_step_bytes_per_fluid_node(Q, D, s, True, pop),
                          "avg_launch_ms": t_step * 1e3,
                          "kernel_share": {"ghost": share[0], "step": share[1], "phi": share[2]}},
             "step_bytes_per_fluid_node": bytes_step,

@@ -50,8 +50,13 @@ typedef enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 } lbm_lattice;
  * a = 1 + eps/2, which is exact algebra and stays accurate at theta -> 90 deg. */
 typedef enum { LBM_GHOST_PRESENT = 0, LBM_GHOST_FAKHARI = 1 } lbm_ghost_rule;
 
-/* Arithmetic and storage type of the whole step. */
-typedef enum { LBM_FP64 = 0, LBM_FP32 = 1 } lbm_precision;
+/* Arithmetic and storage type of the step.  LBM_FP64: double throughout.
+ * LBM_FP32: float arithmetic; populations stored in float as deviations from
+ * the rest state (N_i - chi_i, B_i - chi_i/2), which keeps the small pressure
+ * p = p_h/rho of a dense liquid representable.  LBM_FP32_STORE_FP16: float
+ * arithmetic, the same deviations stored in FP16 scaled by 2^16 (N) and 2^7 (B);
+ * phi, u, p stay float.  Diagnostics reduce in double in every mode. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP32_STORE_FP16 = 2 } lbm_precision;
 
 /* Physical and numerical parameters (lattice units).  The model of Sec. II
  * and Appendix A: phi = 1 is the liquid (heavier) phase, phi = 0 the gas;

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_kern_f32.cu", "lbm_kern_f64.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kern_f32.cu", "lbm_kern_f64.cu", "lbm_kern_f16.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP64 kernels round every multiply and add separately, as the FP64 oracle does.
 EXTRA = {"lbm_kern_f64.cu": ["-fmad=false"]}

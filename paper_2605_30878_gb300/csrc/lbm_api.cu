@@ -25,17 +25,23 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
     int64_t nn = 0, plane = 0;
-    size_t elem = 0;
+    size_t elem = 0;                 // bytes of a field value (phi, u, p, ghost weights)
+    size_t pop_elem = 0;             // bytes of a stored moving population
+    size_t rest_elem = 0;            // bytes of a stored rest population
+    size_t pop_bytes = 0;            // bytes of one population array (Q planes)
     int Q = 0, D = 0, GK = 0;
     size_t off_N[2], off_B[2], off_phi, off_u[2], off_p, off_cls, off_mask, off_gnode, off_gcorner, off_gwt,
-        off_err, off_partial, off_dout;
+        off_err, off_partial, off_dout, off_stage;
     size_t total = 0;
 };
 
 bool make_layout(const lbm_params* P, int64_t ng, Layout& L, std::string& err) {
     if (!P) { err = "params is NULL"; return false; }
     if (P->lattice != LBM_D2Q9 && P->lattice != LBM_D3Q19) { err = "lattice must be 9 (D2Q9) or 19 (D3Q19)"; return false; }
-    if (P->precision != LBM_FP32 && P->precision != LBM_FP64) { err = "precision must be LBM_FP32 or LBM_FP64"; return false; }
+    if (P->precision != LBM_FP32 && P->precision != LBM_FP64 && P->precision != LBM_FP32_STORE_FP16) {
+        err = "precision must be LBM_FP64, LBM_FP32 or LBM_FP32_STORE_FP16";
+        return false;
+    }
     if (P->nx < 1 || P->ny < 1 || P->nz < 1) { err = "grid sizes must be positive"; return false; }
     if (P->lattice == LBM_D2Q9 && P->nz != 1) { err = "D2Q9 needs nz == 1"; return false; }
     if (ng < 0) { err = "n_ghosts must be >= 0"; return false; }
@@ -48,12 +54,15 @@ bool make_layout(const lbm_params* P, int64_t ng, Layout& L, std::string& err) {
         return false;
     }
     L.elem = P->precision == LBM_FP64 ? 8 : 4;
+    L.pop_elem = P->precision == LBM_FP64 ? 8 : (P->precision == LBM_FP32 ? 4 : 2);
+    L.rest_elem = P->precision == LBM_FP64 ? 8 : 4;
     L.Q = P->lattice;
     L.D = P->lattice == LBM_D2Q9 ? 2 : 3;
     L.GK = L.D == 2 ? 4 : 8;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = round_up(o + bytes, ALIGN); return r; };
-    const size_t pop = (size_t)L.Q * L.plane * L.elem;
+    const size_t pop = (size_t)L.plane * (L.rest_elem + (size_t)(L.Q - 1) * L.pop_elem);
+    L.pop_bytes = pop;
     for (int k = 0; k < 2; ++k) { L.off_N[k] = take(pop); L.off_B[k] = take(pop); }
     L.off_phi = take(L.plane * L.elem);
     for (int k = 0; k < 2; ++k) L.off_u[k] = take((size_t)L.D * L.plane * L.elem);
@@ -66,6 +75,7 @@ bool make_layout(const lbm_params* P, int64_t ng, Layout& L, std::string& err) {
     L.off_err = take(16);
     L.off_partial = take((size_t)DIAG_MAX_BLOCKS * DG_REC * 8);
     L.off_dout = take(DG_REC * 8);
+    L.off_stage = take(2 * (size_t)L.plane * L.elem);   // two planes of field-typed values
     L.total = o;
     return true;
 }
@@ -117,6 +127,16 @@ lbm_status fail(lbm_domain* d, lbm_status s, const std::string& msg) {
             return fail(dom, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
     } while (0)
 
+// Call f with a value of the Launch type of the domain's precision.
+template <typename F>
+void dispatch(const lbm_domain* d, F&& f) {
+    switch (d->prm.precision) {
+    case LBM_FP64: f(Launch<double, double>{}); break;
+    case LBM_FP32: f(Launch<float, float>{}); break;
+    default: f(Launch<float, __half>{}); break;
+    }
+}
+
 // Lattice neighbour offsets of a stencil (excluding rest), for node classes.
 void stencil_offsets(int Q, std::vector<int>& ox, std::vector<int>& oy, std::vector<int>& oz) {
     for (int dz = -1; dz <= 1; ++dz)
@@ -138,8 +158,11 @@ void color_weights(int Q, double M_phi, double chi[19], double& alpha, double& c
     for (int i = 0; i < 19; ++i) chi[i] = 0.0;
     chi[0] = alpha;
     for (int i = 1; i < Q; ++i) {
-        const double wi = Q == 9 ? Lattice<9>::w(i) : Lattice<19>::w(i);
-        chi[i] = (1.0 - alpha) * wi / (1.0 - w0);
+        if (Q == 9) {
+            chi[i] = (i <= 4) ? (1.0 - alpha) / 5.0 : (1.0 - alpha) / 20.0;     // Eq. (ChiTerm)
+        } else {
+            chi[i] = (1.0 - alpha) * Lattice<19>::w(i) / (1.0 - w0);          // same rule in 3D
+        }
     }
     c2chi = (1.0 - alpha) * cs2 / (1.0 - w0);
 }
@@ -234,23 +257,19 @@ void launch_one_step(lbm_domain* d, int cur, cudaStream_t s, cudaEvent_t* ev = n
     if (ev) cudaEventRecord(ev[0], s);
     if (d->ng > 0) {
         const void* wt = d->at<void>(L.off_gwt);
-        if (d->fp64)
-            Launch<double>::ghost(L.GK, d->cfg.ghost_rule, d->ng, d->at<int32_t>(L.off_gnode),
-                                  d->at<int32_t>(L.off_gcorner), wt, d->cfg.exp_eps, d->cfg.eps, d->phi(), s);
-        else
-            Launch<float>::ghost(L.GK, d->cfg.ghost_rule, d->ng, d->at<int32_t>(L.off_gnode),
-                                 d->at<int32_t>(L.off_gcorner), wt, d->cfg.exp_eps, d->cfg.eps, d->phi(), s);
+        dispatch(d, [&](auto Lx) {
+            decltype(Lx)::ghost(L.GK, d->cfg.ghost_rule, d->ng, d->at<int32_t>(L.off_gnode),
+                                d->at<int32_t>(L.off_gcorner), wt, d->cfg.exp_eps, d->cfg.eps, d->phi(), s);
+        });
     }
     StepPtrs sp;
     sp.Nin = d->N(cur); sp.Bin = d->B(cur); sp.Nout = d->N(1 - cur); sp.Bout = d->B(1 - cur);
     sp.phi = d->phi(); sp.u_in = d->U(cur); sp.u_out = d->U(1 - cur); sp.p = d->p();
     sp.mask = d->mask(); sp.err = d->errflag();
     if (ev) cudaEventRecord(ev[1], s);
-    if (d->fp64) Launch<double>::step(d->cfg, sp, s);
-    else Launch<float>::step(d->cfg, sp, s);
+    dispatch(d, [&](auto Lx) { decltype(Lx)::step(d->cfg, sp, s); });
     if (ev) cudaEventRecord(ev[2], s);
-    if (d->fp64) Launch<double>::phi(d->cfg, d->B(1 - cur), d->mask(), d->phi(), s);
-    else Launch<float>::phi(d->cfg, d->B(1 - cur), d->mask(), d->phi(), s);
+    dispatch(d, [&](auto Lx) { decltype(Lx)::phi(d->cfg, d->B(1 - cur), d->mask(), d->phi(), s); });
     if (ev) cudaEventRecord(ev[3], s);
 }
 
@@ -310,17 +329,14 @@ lbm_status init_state(lbm_domain* d, int mode, const double ctr[3], double R0) {
     CUDA_TRY(d, cudaMemsetAsync(d->errflag(), 0, sizeof(int), d->stream));
     for (int k = 0; k < 2; ++k) {
         CUDA_TRY(d, cudaMemsetAsync(d->U(k), 0, (size_t)L.D * L.plane * L.elem, d->stream));
-        CUDA_TRY(d, cudaMemsetAsync(d->N(k), 0, (size_t)L.Q * L.plane * L.elem, d->stream));
-        CUDA_TRY(d, cudaMemsetAsync(d->B(k), 0, (size_t)L.Q * L.plane * L.elem, d->stream));
+        CUDA_TRY(d, cudaMemsetAsync(d->N(k), 0, L.pop_bytes, d->stream));
+        CUDA_TRY(d, cudaMemsetAsync(d->B(k), 0, L.pop_bytes, d->stream));
     }
     CUDA_TRY(d, cudaMemsetAsync(d->p(), 0, (size_t)L.plane * L.elem, d->stream));
-    if (d->fp64) {
-        Launch<double>::init_phi(d->cfg, d->cls(), d->phi(), mode, ctr, R0, ghost_value, d->stream);
-        Launch<double>::init_pops(d->cfg, d->cls(), d->phi(), d->N(0), d->B(0), d->stream);
-    } else {
-        Launch<float>::init_phi(d->cfg, d->cls(), d->phi(), mode, ctr, R0, ghost_value, d->stream);
-        Launch<float>::init_pops(d->cfg, d->cls(), d->phi(), d->N(0), d->B(0), d->stream);
-    }
+    dispatch(d, [&](auto Lx) {
+        decltype(Lx)::init_phi(d->cfg, d->cls(), d->phi(), mode, ctr, R0, ghost_value, d->stream);
+        decltype(Lx)::init_pops(d->cfg, d->cls(), d->phi(), d->N(0), d->B(0), d->stream);
+    });
     CUDA_TRY(d, cudaGetLastError());
     return LBM_OK;
 }
@@ -594,10 +610,10 @@ lbm_status lbm_diagnostics(lbm_domain* d, const lbm_probe* probe, lbm_diag* out)
     }
     double* partial = d->at<double>(L.off_partial);
     double* dout = d->at<double>(L.off_dout);
-    if (d->fp64)
-        Launch<double>::diag(d->cfg, d->cls(), d->N(d->cur), d->phi(), d->U(d->cur), d->p(), pr, partial, dout, d->stream);
-    else
-        Launch<float>::diag(d->cfg, d->cls(), d->N(d->cur), d->phi(), d->U(d->cur), d->p(), pr, partial, dout, d->stream);
+    dispatch(d, [&](auto Lx) {
+        decltype(Lx)::diag(d->cfg, d->cls(), d->N(d->cur), d->phi(), d->U(d->cur), d->p(), pr, partial, dout,
+                           d->stream);
+    });
     CUDA_TRY(d, cudaGetLastError());
     double h[DG_REC];
     CUDA_TRY(d, cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, d->stream));
@@ -659,13 +675,13 @@ lbm_status lbm_read_state(lbm_domain* d, int32_t field, double* host_out) {
     switch (field) {
     case LBM_FIELD_N:
     case LBM_FIELD_B: {
-        void* st = field == LBM_FIELD_N ? d->N(d->cur) : d->B(d->cur);
-        void* spare = field == LBM_FIELD_N ? d->N(1 - d->cur) : d->B(1 - d->cur);
-        if (d->fp64) Launch<double>::gather(d->cfg, d->cls(), st, spare, d->stream);
-        else Launch<float>::gather(d->cfg, d->cls(), st, spare, d->stream);
-        CUDA_TRY(d, cudaGetLastError());
+        const bool is_b = field == LBM_FIELD_B;
+        void* st = is_b ? d->B(d->cur) : d->N(d->cur);
+        void* stage = d->at<void>(L.off_stage);
         for (int i = 0; i < L.Q; ++i) {
-            lbm_status s = download(d, host_out + (size_t)i * nn, (const char*)spare + (size_t)i * L.plane * L.elem, nn);
+            dispatch(d, [&](auto Lx) { decltype(Lx)::gather_dir(d->cfg, d->cls(), i, is_b, st, stage, d->stream); });
+            CUDA_TRY(d, cudaGetLastError());
+            lbm_status s = download(d, host_out + (size_t)i * nn, stage, nn);
             if (s != LBM_OK) return s;
         }
         return LBM_OK;
@@ -696,15 +712,20 @@ lbm_status lbm_write_state(lbm_domain* d, int32_t field, const double* host_in) 
     switch (field) {
     case LBM_FIELD_N:
     case LBM_FIELD_B: {
-        void* st = field == LBM_FIELD_N ? d->N(d->cur) : d->B(d->cur);
-        void* spare = field == LBM_FIELD_N ? d->N(1 - d->cur) : d->B(1 - d->cur);
+        const bool is_b = field == LBM_FIELD_B;
+        void* st = is_b ? d->B(d->cur) : d->N(d->cur);
+        char* stage = d->at<char>(L.off_stage);
         for (int i = 0; i < L.Q; ++i) {
-            lbm_status s = upload(d, (char*)spare + (size_t)i * L.plane * L.elem, host_in + (size_t)i * nn, nn);
+            const int o = d->prm.lattice == 9 ? Lattice<9>::opp(i) : Lattice<19>::opp(i);
+            lbm_status s = upload(d, stage, host_in + (size_t)i * nn, nn);
+            if (s == LBM_OK) s = upload(d, stage + (size_t)L.plane * L.elem, host_in + (size_t)o * nn, nn);
             if (s != LBM_OK) return s;
+            dispatch(d, [&](auto Lx) {
+                decltype(Lx)::scatter_dir(d->cfg, d->cls(), i, is_b, stage, stage + (size_t)L.plane * L.elem, st,
+                                          d->stream);
+            });
+            CUDA_TRY(d, cudaGetLastError());
         }
-        if (d->fp64) Launch<double>::scatter(d->cfg, d->cls(), spare, st, d->stream);
-        else Launch<float>::scatter(d->cfg, d->cls(), spare, st, d->stream);
-        CUDA_TRY(d, cudaGetLastError());
         CUDA_TRY(d, cudaStreamSynchronize(d->stream));
         return LBM_OK;
     }
@@ -742,11 +763,12 @@ int32_t lbm_launches_per_step(const lbm_domain* d) { return d ? (d->ng > 0 ? 3 :
 double lbm_bytes_per_fluid_node(const lbm_domain* d) {
     if (!d) return 0.0;
     const double s = (double)d->lay.elem;
-    const int Q = d->lay.Q, D = d->lay.D;
+    const double pop = (double)d->lay.rest_elem + (d->lay.Q - 1) * (double)d->lay.pop_elem;   // per node and array
+    const int D = d->lay.D;
     // populations read + written twice over (N, B); phi written (k_phi) and read (k_step);
     // u written, and read when the density contrast makes F_visc active; p written; the 4-byte
     // bounce-back mask read by k_step and k_phi
-    return 4.0 * Q * s + 2.0 * s + (d->contrast ? 2.0 : 1.0) * D * s + s + 8.0;
+    return 4.0 * pop + 2.0 * s + (d->contrast ? 2.0 : 1.0) * D * s + s + 8.0;
 }
 
 int64_t lbm_fluid_nodes(const lbm_domain* d) { return d ? d->n_fluid : 0; }

@@ -57,11 +57,13 @@ __global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restric
 }
 
 // Populations at t = 0: post-streaming N_i = chi_i, B_i = phi chi_i, written in
-// the pull layout (the value a later pull at x + c_i reads sits at x).
-template <int Q, typename T>
+// the pull layout (the value a later pull at x + c_i reads sits at x) and in
+// the storage form of S (full values, or deviations N - chi_i, B - chi_i/2).
+template <int Q, typename T, typename S>
 __global__ void k_init_pops(Dims d, StepParams<T> P, const uint8_t* __restrict__ cls, const T* __restrict__ phi,
-                            T* __restrict__ Nst, T* __restrict__ Bst) {
+                            S* __restrict__ Nst, S* __restrict__ Bst) {
     using L = Lattice<Q>;
+    constexpr bool kShift = PopStore<S>::kShift;
     const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {
@@ -72,15 +74,18 @@ __global__ void k_init_pops(Dims d, StepParams<T> P, const uint8_t* __restrict__
         for (int i = 0; i < Q; ++i) {
             const int64_t dn = shifted(d, x, y, z, L::cx(i), L::cy(i), L::cz(i));
             const T ph = (cls[dn] == CLS_FLUID) ? phi[dn] : phi[node];
-            Nst[i * d.plane + node] = P.chi[i];
-            Bst[i * d.plane + node] = ph * P.chi[i];
+            const int pl = (int)d.plane, nd = (int)node;
+            pop_store<S, T>(Nst, i, pl, nd, kShift ? T(0) : P.chi[i], kScaleN);
+            pop_store<S, T>(Bst, i, pl, nd, kShift ? (ph - T(0.5)) * P.chi[i] : ph * P.chi[i], kScaleB);
         }
     }
 }
 
-// post-streaming values -> pull layout (inverse of k_gather)
-template <int Q, typename T>
-__global__ void k_scatter(Dims d, const uint8_t* __restrict__ cls, const T* __restrict__ post, T* __restrict__ st) {
+// One direction i of post-streaming values -> pull layout: st_i[y] = post_i[y + c_i]
+// if y + c_i is fluid, else post_opp[y]; stored as value - base (base = 0, chi_i or chi_i/2).
+template <int Q, typename T, typename S>
+__global__ void k_scatter_dir(Dims d, const uint8_t* __restrict__ cls, int i, const T* __restrict__ post_i,
+                              const T* __restrict__ post_opp, T base, float scale, S* __restrict__ st) {
     using L = Lattice<Q>;
     const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
@@ -88,33 +93,30 @@ __global__ void k_scatter(Dims d, const uint8_t* __restrict__ cls, const T* __re
         if (cls[node] != CLS_FLUID) continue;
         int x, y, z;
         node_xyz(node, d, x, y, z);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int64_t dn = shifted(d, x, y, z, L::cx(i), L::cy(i), L::cz(i));
-            st[i * d.plane + node] = (cls[dn] == CLS_FLUID) ? post[i * d.plane + dn] : post[L::opp(i) * d.plane + node];
-        }
+        const int64_t dn = shifted(d, x, y, z, L::cx(i), L::cy(i), L::cz(i));
+        const T v = (cls[dn] == CLS_FLUID) ? post_i[dn] : post_opp[node];
+        pop_store<S, T>(st, i, (int)d.plane, (int)node, v - base, scale);
     }
 }
 
-// pull layout -> post-streaming values (0 at solid nodes)
-template <int Q, typename T>
-__global__ void k_gather(Dims d, const uint8_t* __restrict__ cls, const T* __restrict__ st, T* __restrict__ post) {
+// One direction i of the pull layout -> post-streaming values (0 at solid nodes).
+template <int Q, typename T, typename S>
+__global__ void k_gather_dir(Dims d, const uint8_t* __restrict__ cls, int i, const S* __restrict__ st, T base,
+                             float scale, T* __restrict__ post) {
     using L = Lattice<Q>;
     const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {
-        const bool fluid = cls[node] == CLS_FLUID;
-        int x, y, z;
-        node_xyz(node, d, x, y, z);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            T v = T(0);
-            if (fluid) {
-                const int64_t sn = shifted(d, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
-                v = (cls[sn] == CLS_FLUID) ? st[i * d.plane + sn] : st[L::opp(i) * d.plane + node];
-            }
-            post[i * d.plane + node] = v;
+        T v = T(0);
+        if (cls[node] == CLS_FLUID) {
+            int x, y, z;
+            node_xyz(node, d, x, y, z);
+            const int64_t sn = shifted(d, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
+            const bool from_fluid = cls[sn] == CLS_FLUID;
+            v = base + pop_load<S, T>(st, from_fluid ? i : L::opp(i), (int)d.plane, (int)(from_fluid ? sn : node),
+                                      scale);
         }
+        post[node] = v;
     }
 }
 
@@ -138,10 +140,10 @@ struct ProbeDev {
     double center[3], radius, normal[3], exclude;
 };
 
-template <int Q, typename T>
+template <int Q, typename T, typename S>
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rho_l, double rho_g,
-                                                               const uint8_t* __restrict__ cls,
-                                                               const T* __restrict__ Nst, const T* __restrict__ phi,
+                                                               const uint8_t* __restrict__ cls, StepParams<T> P,
+                                                               const S* __restrict__ Nst, const T* __restrict__ phi,
                                                                const T* __restrict__ u, const T* __restrict__ p,
                                                                ProbeDev pr, double* __restrict__ partial) {
     using L = Lattice<Q>;
@@ -164,7 +166,10 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rh
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int64_t sn = shifted(d, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
-            ps += (double)((cls[sn] == CLS_FLUID) ? Nst[i * d.plane + sn] : Nst[L::opp(i) * d.plane + node]);
+            const bool from_fluid = cls[sn] == CLS_FLUID;
+            ps += pop_load<S, double>(Nst, from_fluid ? i : L::opp(i), (int)d.plane, (int)(from_fluid ? sn : node),
+                                      kScaleN) +
+                  (PopStore<S>::kShift ? (double)P.chi[i] : 0.0);
         }
         acc[DG_POP] += ps;
         double u2 = 0.0;

@@ -1,6 +1,6 @@
-// FP32 instantiation of every kernel launcher.
+// FP32 arithmetic and storage: instantiation of every kernel launcher.
 #include "lbm_launch.cuh"
 
 namespace lbmgpu {
-template struct Launch<float>;
+template struct Launch<float, float>;
 }  // namespace lbmgpu

@@ -1,6 +1,6 @@
-// FP64 instantiation of every kernel launcher.
+// FP64 arithmetic and storage: instantiation of every kernel launcher.
 #include "lbm_launch.cuh"
 
 namespace lbmgpu {
-template struct Launch<double>;
+template struct Launch<double, double>;
 }  // namespace lbmgpu

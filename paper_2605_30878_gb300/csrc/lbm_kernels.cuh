@@ -26,6 +26,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lbm_lattice.cuh"
@@ -40,7 +41,8 @@ struct StepParams {
     int64_t plane;           // elements between consecutive planes of a field
     T rho_l, rho_g, drho;    // drho = rho_l - rho_g
     T inv_nu_l, inv_nu_g;    // 1/nu_l, 1/nu_g
-    T sigma;
+    T sigma, W;
+    T nu_l, nu_g;            // kinematic viscosities
     T k48W, k3W2, two_over_W;   // 48/W, 3W/2, 2/W
     T g[3];
     T chi[19];
@@ -48,12 +50,74 @@ struct StepParams {
     T exp_eps;               // exp(eps), eps = -(4/W) cos(theta)
 };
 
-template <typename T>
+// Population storage.  S = double: full values (FP64 mode, rounding as the
+// oracle).  S = float: deviations from the rest state, N_i - chi_i and
+// B_i - chi_i/2 (FP32 mode); the step computes directly in these deviations,
+// an exact rewrite because sum chi = 1, sum c chi = 0 and chi is isotropic, and
+// it keeps the small pressure of a dense liquid (p = p_h/rho ~ 1e-8 at density
+// ratio 1000) representable.  S = __half: the same deviations, the rest
+// populations (i = 0, whose B deviation reaches chi_0/2 ~ 0.46) as float in the
+// first plane, the moving ones times 2^16 (N) and 2^7 (B) as FP16 in the
+// following Q-1 planes.
+constexpr float kScaleN = 65536.0f;
+constexpr float kScaleB = 128.0f;
+
+// Each array holds the rest plane (direction 0) followed by the Q-1 moving
+// planes; rest(p) and moving(p, plane) return typed pointers to the two parts,
+// moving direction d >= 1 lives at moving + (d - 1) * plane.
+template <typename S> struct PopStore;
+template <typename V> struct PlainStore {
+    static constexpr int kRestBytes = sizeof(V), kMovingBytes = sizeof(V);
+    using Rest = V;
+    using Moving = V;
+    __device__ static const V* rest(const V* p) { return p; }
+    __device__ static V* rest(V* p) { return p; }
+    __device__ static const V* moving(const V* p, int plane) { return p + plane; }
+    __device__ static V* moving(V* p, int plane) { return p + plane; }
+    __device__ static V load_rest(const V* r, int idx) { return __ldg(r + idx); }
+    __device__ static V load_moving(const V* m, int idx, float) { return __ldg(m + idx); }
+    __device__ static void store_rest(V* r, int idx, V v) { r[idx] = v; }
+    __device__ static void store_moving(V* m, int idx, V v, float) { m[idx] = v; }
+};
+template <> struct PopStore<double> : PlainStore<double> { static constexpr bool kShift = false; };
+template <> struct PopStore<float> : PlainStore<float> { static constexpr bool kShift = true; };
+template <> struct PopStore<__half> {
+    static constexpr bool kShift = true;
+    static constexpr int kRestBytes = 4, kMovingBytes = 2;
+    __device__ static const float* rest(const __half* p) { return reinterpret_cast<const float*>(p); }
+    __device__ static float* rest(__half* p) { return reinterpret_cast<float*>(p); }
+    __device__ static const __half* moving(const __half* p, int plane) { return p + 2 * plane; }
+    __device__ static __half* moving(__half* p, int plane) { return p + 2 * plane; }
+    __device__ static float load_rest(const float* r, int idx) { return __ldg(r + idx); }
+    __device__ static float load_moving(const __half* m, int idx, float scale) {
+        return __half2float(__ldg(m + idx)) * (1.0f / scale);
+    }
+    __device__ static void store_rest(float* r, int idx, float v) { r[idx] = v; }
+    __device__ static void store_moving(__half* m, int idx, float v, float scale) {
+        m[idx] = __float2half_rn(v * scale);
+    }
+};
+
+// Runtime-direction access, for the initialisation and state-transfer kernels.
+template <typename S, typename V>
+__device__ __forceinline__ V pop_load(const S* p, int d, int plane, int node, float scale) {
+    using PS = PopStore<S>;
+    if (d == 0) return (V)PS::load_rest(PS::rest(p), node);
+    return (V)PS::load_moving(PS::moving(p, plane), (d - 1) * plane + node, scale);
+}
+template <typename S, typename V>
+__device__ __forceinline__ void pop_store(S* p, int d, int plane, int node, V v, float scale) {
+    using PS = PopStore<S>;
+    if (d == 0) PS::store_rest(PS::rest(p), node, v);
+    else PS::store_moving(PS::moving(p, plane), (d - 1) * plane + node, v, scale);
+}
+
+template <typename T, typename S>
 struct StepBuffers {
-    const T* Nin;
-    const T* Bin;
-    T* Nout;
-    T* Bout;
+    const S* Nin;
+    const S* Bin;
+    S* Nout;
+    S* Bout;
     T* phi;
     const T* u_in;           // velocity of the previous step (F_visc stencil)
     T* u_out;
@@ -118,21 +182,28 @@ struct Wrap {
 template <int Q, typename T, bool LOAD_U>
 __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __restrict__ phi,
                                           const T* __restrict__ u, T* s_phi, T* s_u, int x0, int y0, int z0) {
+    // one warp per halo row (fixed hy, hz): the row's periodic y/z image is
+    // computed once, lanes walk the row's HX consecutive x positions
     using Tl = Tile<Q>;
     constexpr int D = Tl::D;
+    constexpr int ROWS = Tl::HY * Tl::HZ;
+    constexpr int WARPS = Tl::THREADS / 32;
     const int tid = threadIdx.x + Tl::TX * (threadIdx.y + Tl::TY * threadIdx.z);
-    for (int k = tid; k < Tl::HN; k += Tl::THREADS) {
-        const int hx = k % Tl::HX;
-        const int hy = (k / Tl::HX) % Tl::HY;
-        const int hz = k / (Tl::HX * Tl::HY);
-        const int gx = wrap_halo(x0 + hx - 1, P.nx);
+    const int warp = tid >> 5, lane = tid & 31;
+    const int uplane = (int)P.plane;
+    for (int r = warp; r < ROWS; r += WARPS) {
+        const int hy = r % Tl::HY, hz = r / Tl::HY;
         const int gy = wrap_halo(y0 + hy - 1, P.ny);
         const int gz = (D == 2) ? 0 : wrap_halo(z0 + hz - 1, P.nz);
-        const int node = gx + P.nx * (gy + P.ny * gz);
-        s_phi[k] = phi[node];
-        if (LOAD_U) {
+        const int rowbase = P.nx * (gy + P.ny * gz);
+        const int sbase = Tl::HX * r;
+        for (int e = lane; e < Tl::HX; e += 32) {
+            const int node = rowbase + wrap_halo(x0 + e - 1, P.nx);
+            s_phi[sbase + e] = phi[node];
+            if (LOAD_U) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) s_u[d * Tl::HN + k] = u[d * (int)P.plane + node];
+                for (int d = 0; d < D; ++d) s_u[d * Tl::HN + sbase + e] = u[d * uplane + node];
+            }
         }
     }
 }
@@ -140,8 +211,8 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __res
 // ---------------------------------------------------------------------------
 // k_phi: Eq. (phiUpdate) on pulled B*
 // ---------------------------------------------------------------------------
-template <int Q, typename T>
-__global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const T* __restrict__ Bst,
+template <int Q, typename T, typename S>
+__global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const S* __restrict__ Bst,
                                                           const uint32_t* __restrict__ mask, T* __restrict__ phi) {
     using L = Lattice<Q>;
     using Tl = Tile<Q>;
@@ -154,14 +225,17 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const
     if (m & MASK_NOT_FLUID) return;
     const Wrap W(x, y, z, P.nx, P.ny, P.nz);
     const int pl = (int)P.plane;
-    T s = T(0);
+    using PS = PopStore<S>;
+    const auto* mv = PS::moving(Bst, pl);
+    T s = (T)PS::load_rest(PS::rest(Bst), node);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int src = ((m >> i) & 1u) ? L::opp(i) * pl + node
-                                        : i * pl + node + W.off(-L::cx(i), -L::cy(i), -L::cz(i));
-        s += __ldg(Bst + src);
+    for (int i = 1; i < Q; ++i) {
+        const int idx = ((m >> i) & 1u) ? (L::opp(i) - 1) * pl + node
+                                        : (i - 1) * pl + node + W.off(-L::cx(i), -L::cy(i), -L::cz(i));
+        s += (T)PS::load_moving(mv, idx, kScaleB);
     }
-    phi[node] = s;
+    // stored deviations B_i - chi_i/2 sum to phi - 1/2
+    phi[node] = PopStore<S>::kShift ? T(0.5) + s : s;
 }
 
 // ---------------------------------------------------------------------------
@@ -192,10 +266,127 @@ __global__ void __launch_bounds__(256) k_ghost(int64_t n_ghosts, const int32_t* 
 // ---------------------------------------------------------------------------
 // k_step: stencils, forces, macroscopic fields, collision, segregation
 // ---------------------------------------------------------------------------
-template <typename T> __device__ __forceinline__ T rcp(T v) { return T(1) / v; }
+// Reciprocals: FP64 divides exactly, as the oracle; FP32 uses the correctly
+// rounded hardware-assisted reciprocal and reciprocal square root.
+__device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
+__device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double inv_norm_floor(double g2, double floor) {
+    const double gn = sqrt(g2);
+    return 1.0 / (gn > floor ? gn : floor);
+}
+__device__ __forceinline__ float inv_norm_floor(float g2, float floor) {
+    return rsqrtf(g2 > floor * floor ? g2 : floor * floor);
+}
 
-template <int Q, typename T, bool CONTRAST>
-__global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, StepBuffers<T> b) {
+// FP64 node update written in the order the model is stated (Sec. II and
+// Appendix A), as the FP64 oracle evaluates it, so that FP64 results follow the
+// oracle to rounding; only the collision uses its closed form.  Inputs are the
+// lattice-order sums gs[a] = sum w c_a phi, ls = sum w (phi_i - phi),
+// us[a][b] = sum w c_a u_b.
+template <int Q, bool CONTRAST>
+__device__ __forceinline__ void node_update_literal(const StepParams<double>& P, const double* N, double phi,
+                                                    const double* gs, double ls, const double (*us)[3], double* Nst,
+                                                    double* Bst, double* u, double& p) {
+    using L = Lattice<Q>;
+    constexpr int D = L::D;
+    const double cs2 = 1.0 / 3.0;
+    const double w0 = L::w(0);
+    double gphi[3], gu[3][3];
+    for (int a = 0; a < 3; ++a) {
+        gphi[a] = gs[a] / cs2;
+        for (int c = 0; c < 3; ++c) gu[a][c] = us[a][c] / cs2;
+    }
+    const double lap = ls * (2.0 / cs2);
+    const double rho = P.rho_l * phi + P.rho_g * (1.0 - phi);
+    double grho[3];
+    for (int a = 0; a < 3; ++a) grho[a] = (P.rho_l - P.rho_g) * gphi[a];
+    const double nu = 1.0 / (phi / P.nu_l + (1.0 - phi) / P.nu_g);
+    const double tau = 0.5 + nu / cs2;
+    // force-free velocity and its pressure (Eq. pressureUpdate) for F_p
+    double u0[3] = {0.0, 0.0, 0.0};
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (L::cx(i)) u0[0] += N[i] * L::cx(i);
+        if (L::cy(i)) u0[1] += N[i] * L::cy(i);
+        if (L::cz(i)) u0[2] += N[i] * L::cz(i);
+        if (i > 0) s += N[i];
+    }
+    const double uu0 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+    const double p0 = (-(w0 / 2.0) * uu0 - (1.0 - P.chi[0]) * cs2 + s * cs2) / (1.0 - w0);
+    // Eqs. (surfaceTensionForce), body force, (pressCorrection), (viscCorrection), (totalForce)
+    const double mu = (48.0 / P.W) * phi * (1.0 - phi) * (phi - 0.5) + (3.0 * P.W / 2.0) * lap;
+    double F[3];
+    for (int a = 0; a < 3; ++a) {
+        const double Fs = -P.sigma * mu * gphi[a];
+        const double Fb = rho * P.g[a];
+        double Fp = 0.0, Fv = 0.0;
+        if (CONTRAST) {
+            Fp = -p0 * grho[a];
+            for (int c = 0; c < 3; ++c) Fv += (gu[a][c] + gu[c][a]) * grho[c];
+            Fv *= cs2 * (tau - 0.5);
+        }
+        F[a] = Fv + Fp + Fs + Fb;
+    }
+    if (D == 2) F[2] = 0.0;
+    // Eqs. (velUpdate), (pressureUpdate)
+    for (int a = 0; a < 3; ++a) u[a] = u0[a] + F[a] / (2.0 * rho);
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    p = (-(w0 / 2.0) * uu - (1.0 - P.chi[0]) * cs2 + s * cs2) / (1.0 - w0);
+    // Eq. (equilibriumDistribution), Eq. (forceGuo)
+    double neq[Q], Fi[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const double cu = L::cx(i) * u[0] + L::cy(i) * u[1] + L::cz(i) * u[2];
+        if (i == 0) neq[i] = P.chi[0] - (1.0 - w0) * p / cs2 - w0 * uu / (2.0 * cs2);
+        else neq[i] = P.chi[i] + L::w(i) * (p / cs2 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+        const double cF = L::cx(i) * F[0] + L::cy(i) * F[1] + L::cz(i) * F[2];
+        Fi[i] = (L::w(i) / cs2) * cF / rho;
+    }
+    // Eq. (MRTCOLL) in closed form: N* = Neq + F_i/2 + (1 - 1/tau) sum_k m_k (m_k . (N - Neq)) / |m_k|^2
+    // over the traceless second-order rows m_k
+    double mf[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const double f = N[i] - neq[i];
+        if (D == 2) {
+            mf[0] += (cx * cx - cy * cy) * f;
+            mf[1] += (cx * cy) * f;
+        } else {
+            const int c2 = cx * cx + cy * cy + cz * cz;
+            mf[0] += (3 * cx * cx - c2) * f;
+            mf[1] += (cy * cy - cz * cz) * f;
+            mf[2] += (cx * cy) * f;
+            mf[3] += (cy * cz) * f;
+            mf[4] += (cx * cz) * f;
+        }
+    }
+    const double om = 1.0 - 1.0 / tau;
+    // segregation, Eq. (segragationStepBlue), n_phi = grad phi / max(|grad phi|, 1e-6)
+    const double gn = sqrt(gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2]);
+    double n[3];
+    for (int a = 0; a < 3; ++a) n[a] = gphi[a] / (gn > 1e-6 ? gn : 1e-6);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        double proj;
+        if (D == 2) {
+            proj = (cx * cx - cy * cy) * mf[0] / 4.0 + (cx * cy) * mf[1] / 4.0;
+        } else {
+            const int c2 = cx * cx + cy * cy + cz * cz;
+            proj = (3 * cx * cx - c2) * mf[0] / 36.0 + (cy * cy - cz * cz) * mf[1] / 12.0 + (cx * cy) * mf[2] / 4.0 +
+                   (cy * cz) * mf[3] / 4.0 + (cx * cz) * mf[4] / 4.0;
+        }
+        Nst[i] = neq[i] + 0.5 * Fi[i] + om * proj;
+        const double cn = cx * n[0] + cy * n[1] + cz * n[2];
+        const double neq0 = P.chi[i] + L::w(i) * (p / cs2);
+        Bst[i] = phi * Nst[i] + 2.0 * (cn / P.W) * phi * (1.0 - phi) * neq0;
+    }
+}
+
+template <int Q, typename T, typename S, bool CONTRAST>
+__global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, StepBuffers<T, S> b) {
     using L = Lattice<Q>;
     using Tl = Tile<Q>;
     constexpr int D = L::D;
@@ -215,12 +406,19 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
 
     // pull the post-streaming populations N (bounce-back where x - c_i is solid);
     // B enters the collision only through phi = sum B, which k_phi computed
+    // (full values for FP64 storage, deviations N_i - chi_i otherwise)
+    using PS = PopStore<S>;
+    constexpr bool kShift = PS::kShift;
     T N[Q];
+    N[0] = (T)PS::load_rest(PS::rest(b.Nin), node);
+    {
+        const auto* mv = PS::moving(b.Nin, pl);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int src = ((m >> i) & 1u) ? L::opp(i) * pl + node
-                                        : i * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i));
-        N[i] = __ldg(b.Nin + src);
+        for (int i = 1; i < Q; ++i) {
+            const int idx = ((m >> i) & 1u) ? (L::opp(i) - 1) * pl + node
+                                            : (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i));
+            N[i] = (T)PS::load_moving(mv, idx, kScaleN);
+        }
     }
 
     // isotropic stencils: grad f = 3 sum_i w_i c_i f(x+c_i), lap f = 6 sum_i w_i (f(x+c_i) - f(x)).
@@ -273,6 +471,24 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
         }
     }
     constexpr double w0 = L::w(0);
+    if constexpr (sizeof(T) == 8) {
+        double Ns[Q], Bs[Q], u[3], p;
+        node_update_literal<Q, CONTRAST>(P, N, phi, gp, lsum, du, Ns, Bs, u, p);
+        PS::store_rest(PS::rest(b.Nout), node, Ns[0]);
+        PS::store_rest(PS::rest(b.Bout), node, Bs[0]);
+        auto* Nmv = PS::moving(b.Nout, pl);
+        auto* Bmv = PS::moving(b.Bout, pl);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            PS::store_moving(Nmv, (i - 1) * pl + node, Ns[i], kScaleN);
+            PS::store_moving(Bmv, (i - 1) * pl + node, Bs[i], kScaleB);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
+        b.p[node] = p;
+        if (!(u[0] * u[0] + u[1] * u[1] + u[2] * u[2] < 1e30)) atomicOr(b.err, 1);
+        return;
+    } else {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         gp[a] *= T(3);
@@ -294,21 +510,35 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        sum_moving += N[i];
-        if (cx > 0) { u0[0] += N[i]; Pxx += N[i]; }
-        if (cx < 0) { u0[0] -= N[i]; Pxx += N[i]; }
-        if (cy > 0) { u0[1] += N[i]; Pyy += N[i]; }
-        if (cy < 0) { u0[1] -= N[i]; Pyy += N[i]; }
-        if (cz > 0) { u0[2] += N[i]; Pzz += N[i]; }
-        if (cz < 0) { u0[2] -= N[i]; Pzz += N[i]; }
-        if (cx * cy > 0) Pxy += N[i];
-        if (cx * cy < 0) Pxy -= N[i];
-        if (cx * cz > 0) Pxz += N[i];
-        if (cx * cz < 0) Pxz -= N[i];
-        if (cy * cz > 0) Pyz += N[i];
-        if (cy * cz < 0) Pyz -= N[i];
+        if (kPairs) {
+            // odd moments from N_i - N_opp, even ones from N_i + N_opp
+            if (L::opp(i) < i) continue;
+            const T sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
+            sum_moving += sp;
+            if (cx) { u0[0] += T(cx) * dp; Pxx += sp; }
+            if (cy) { u0[1] += T(cy) * dp; Pyy += sp; }
+            if (cz) { u0[2] += T(cz) * dp; Pzz += sp; }
+            if (cx * cy) Pxy += T(cx * cy) * sp;
+            if (cx * cz) Pxz += T(cx * cz) * sp;
+            if (cy * cz) Pyz += T(cy * cz) * sp;
+        } else {
+            sum_moving += N[i];
+            if (cx > 0) { u0[0] += N[i]; Pxx += N[i]; }
+            if (cx < 0) { u0[0] -= N[i]; Pxx += N[i]; }
+            if (cy > 0) { u0[1] += N[i]; Pyy += N[i]; }
+            if (cy < 0) { u0[1] -= N[i]; Pyy += N[i]; }
+            if (cz > 0) { u0[2] += N[i]; Pzz += N[i]; }
+            if (cz < 0) { u0[2] -= N[i]; Pzz += N[i]; }
+            if (cx * cy > 0) Pxy += N[i];
+            if (cx * cy < 0) Pxy -= N[i];
+            if (cx * cz > 0) Pxz += N[i];
+            if (cx * cz < 0) Pxz -= N[i];
+            if (cy * cz > 0) Pyz += N[i];
+            if (cy * cz < 0) Pyz -= N[i];
+        }
     }
-    const T pres_base = (sum_moving - (T(1) - P.chi[0])) * T(1.0 / 3.0);
+    // sum_{i>0} chi_i = 1 - chi_0: with deviations the chi part is already gone
+    const T pres_base = kShift ? sum_moving * T(1.0 / 3.0) : (sum_moving - (T(1) - P.chi[0])) * T(1.0 / 3.0);
     const T inv_1mw0 = T(1.0 / (1.0 - w0));
     const T uu0 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
     const T p0 = (pres_base - T(0.5 * w0) * uu0) * inv_1mw0;
@@ -357,32 +587,29 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     }
 
     // segregation: n_phi = grad phi / max(|grad phi|, 1e-6)
-    const T gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
-    const T inv_gn = rcp(gn > T(1e-6) ? gn : T(1e-6));
+    const T inv_gn = inv_norm_floor(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2], T(1e-6));
     const T kseg = P.two_over_W * phi * (T(1) - phi) * inv_gn;
     const T three_p = T(3) * p;
     const T halfF = T(1.5) * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
     const T base0 = T(3) * u[0], base1 = T(3) * u[1], base2 = T(3) * u[2];
     const T common = three_p - T(1.5) * uu;
 
-    T* __restrict__ Nout = b.Nout;
-    T* __restrict__ Bout = b.Bout;
+    auto* __restrict__ Nrest = PS::rest(b.Nout);
+    auto* __restrict__ Brest = PS::rest(b.Bout);
+    auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
+    auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
+    // rest direction: no forcing, no stress projection, no recoloring (c_0 = 0)
+    {
+        const T nst = (kShift ? T(0) : P.chi[0]) - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
+        const T bst = kShift ? phi * nst + (phi - T(0.5)) * P.chi[0] : phi * nst;
+        PS::store_rest(Nrest, node, nst);
+        PS::store_rest(Brest, node, bst);
+    }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 1; i < Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const T wi = T(L::w(i));
-        T neq, nst;
-        if (i == 0) {
-            neq = P.chi[0] - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
-            nst = neq;
-        } else {
-            T cu3 = T(0), cF = T(0);   // 3 c.u and c.F
-            if (cx) { cu3 += T(cx) * base0; cF += T(cx) * F[0]; }
-            if (cy) { cu3 += T(cy) * base1; cF += T(cy) * F[1]; }
-            if (cz) { cu3 += T(cz) * base2; cF += T(cz) * F[2]; }
-            neq = P.chi[i] + wi * (common + cu3 + T(0.5) * cu3 * cu3);
-            nst = neq + wi * halfF * cF;
-        }
+        const T chi_i = kShift ? T(0) : P.chi[i];      // the rest-state part carried in N
         T proj;
         if (D == 2) {
             proj = T(cx * cx - cy * cy) * A0 + T(cx * cy) * Axy;
@@ -391,22 +618,37 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
             proj = T(3 * cx * cx - c2) * A0 + T(cy * cy - cz * cz) * A1 + T(cx * cy) * Axy + T(cx * cz) * Axz +
                    T(cy * cz) * Ayz;
         }
-        nst += proj;
-        T bst = phi * nst;
-        if (i != 0) {
-            T cg = T(0);
-            if (cx) cg += T(cx) * gp[0];
-            if (cy) cg += T(cy) * gp[1];
-            if (cz) cg += T(cz) * gp[2];
-            bst += kseg * cg * (P.chi[i] + wi * three_p);
+        T cu3 = T(0), cF = T(0), cg = T(0);   // 3 c.u, c.F, c.grad phi
+        if (cx) { cu3 += T(cx) * base0; cF += T(cx) * F[0]; cg += T(cx) * gp[0]; }
+        if (cy) { cu3 += T(cy) * base1; cF += T(cy) * F[1]; cg += T(cy) * gp[1]; }
+        if (cz) { cu3 += T(cz) * base2; cF += T(cz) * F[2]; cg += T(cz) * gp[2]; }
+        const T rc = kseg * cg * (P.chi[i] + wi * three_p);     // recoloring, odd in c
+        if (kPairs) {
+            // direction i and its opposite share the even part and flip the odd part
+            if (L::opp(i) < i) continue;
+            const int o = L::opp(i);
+            const T even = chi_i + wi * (common + T(0.5) * cu3 * cu3) + proj;
+            const T odd = wi * (cu3 + halfF * cF);
+            const T ni = even + odd, no = even - odd;
+            const T shift_b = kShift ? (phi - T(0.5)) * P.chi[i] : T(0);
+            PS::store_moving(Nmov, (i - 1) * pl + node, ni, kScaleN);
+            PS::store_moving(Nmov, (o - 1) * pl + node, no, kScaleN);
+            PS::store_moving(Bmov, (i - 1) * pl + node, phi * ni + shift_b + rc, kScaleB);
+            PS::store_moving(Bmov, (o - 1) * pl + node, phi * no + shift_b - rc, kScaleB);
+        } else {
+            const T neq = chi_i + wi * (common + cu3 + T(0.5) * cu3 * cu3);
+            const T nst = neq + wi * halfF * cF + proj;
+            // B* = phi N* + recolor; stored as B* - chi_i/2 = phi dN* + (phi - 1/2) chi_i + recolor
+            const T bst = (kShift ? phi * nst + (phi - T(0.5)) * P.chi[i] : phi * nst) + rc;
+            PS::store_moving(Nmov, (i - 1) * pl + node, nst, kScaleN);
+            PS::store_moving(Bmov, (i - 1) * pl + node, bst, kScaleB);
         }
-        Nout[i * pl + node] = nst;
-        Bout[i * pl + node] = bst;
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
     b.p[node] = p;
     if (!(uu < T(1e30))) atomicOr(b.err, 1);   // also catches NaN
+    }
 }
 
 }  // namespace lbmgpu

@@ -1,5 +1,7 @@
-// Typed kernel launchers.  lbm_kern_f32.cu and lbm_kern_f64.cu instantiate
-// Launch<float> and Launch<double>; the host API only sees these functions.
+// Typed kernel launchers: T is the arithmetic type, S the population storage
+// type.  lbm_kern_f64.cu, lbm_kern_f32.cu and lbm_kern_f16.cu instantiate
+// Launch<double, double>, Launch<float, float> and Launch<float, __half>; the
+// host API only sees these functions.
 #pragma once
 
 #include <cstdint>
@@ -37,7 +39,7 @@ struct StepPtrs {
     int* err;
 };
 
-template <typename T>
+template <typename T, typename S>
 struct Launch {
     static StepParams<T> params(const StepConfig& c) {
         StepParams<T> P;
@@ -46,6 +48,8 @@ struct Launch {
         P.rho_l = (T)c.rho_l; P.rho_g = (T)c.rho_g; P.drho = (T)(c.rho_l - c.rho_g);
         P.inv_nu_l = (T)(1.0 / c.nu_l); P.inv_nu_g = (T)(1.0 / c.nu_g);
         P.sigma = (T)c.sigma;
+        P.W = (T)c.W;
+        P.nu_l = (T)c.nu_l; P.nu_g = (T)c.nu_g;
         P.k48W = (T)(48.0 / c.W); P.k3W2 = (T)(1.5 * c.W); P.two_over_W = (T)(2.0 / c.W);
         for (int a = 0; a < 3; ++a) P.g[a] = (T)c.g[a];
         for (int i = 0; i < 19; ++i) P.chi[i] = (T)c.chi[i];
@@ -68,14 +72,14 @@ struct Launch {
     template <int Q>
     static void step_q(const StepConfig& c, const StepPtrs& p, cudaStream_t s) {
         const StepParams<T> P = params(c);
-        StepBuffers<T> b;
-        b.Nin = (const T*)p.Nin; b.Bin = (const T*)p.Bin; b.Nout = (T*)p.Nout; b.Bout = (T*)p.Bout;
+        StepBuffers<T, S> b;
+        b.Nin = (const S*)p.Nin; b.Bin = (const S*)p.Bin; b.Nout = (S*)p.Nout; b.Bout = (S*)p.Bout;
         b.phi = (T*)p.phi; b.u_in = (const T*)p.u_in; b.u_out = (T*)p.u_out; b.p = (T*)p.p;
         b.mask = p.mask; b.err = p.err;
         if (c.contrast)
-            k_step<Q, T, true><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
+            k_step<Q, T, S, true><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
         else
-            k_step<Q, T, false><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
+            k_step<Q, T, S, false><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
     }
     static void step(const StepConfig& c, const StepPtrs& p, cudaStream_t s) {
         if (c.Q == 9) step_q<9>(c, p, s); else step_q<19>(c, p, s);
@@ -84,9 +88,9 @@ struct Launch {
     static void phi(const StepConfig& c, const void* Bst, const uint32_t* mask, void* phi, cudaStream_t s) {
         const StepParams<T> P = params(c);
         if (c.Q == 9)
-            k_phi<9, T><<<step_grid<9>(c.d), step_block<9>(), 0, s>>>(P, (const T*)Bst, mask, (T*)phi);
+            k_phi<9, T, S><<<step_grid<9>(c.d), step_block<9>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi);
         else
-            k_phi<19, T><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const T*)Bst, mask, (T*)phi);
+            k_phi<19, T, S><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi);
     }
 
     static void ghost(int GK, int rule, int64_t ng, const int32_t* node, const int32_t* corner, const void* wt,
@@ -119,23 +123,37 @@ struct Launch {
     static void init_pops(const StepConfig& c, const uint8_t* cls, const void* phi, void* N, void* B, cudaStream_t s) {
         const StepParams<T> P = params(c);
         if (c.Q == 9)
-            k_init_pops<9, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, P, cls, (const T*)phi, (T*)N, (T*)B);
+            k_init_pops<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, P, cls, (const T*)phi, (S*)N, (S*)B);
         else
-            k_init_pops<19, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, P, cls, (const T*)phi, (T*)N, (T*)B);
+            k_init_pops<19, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, P, cls, (const T*)phi, (S*)N, (S*)B);
     }
 
-    static void scatter(const StepConfig& c, const uint8_t* cls, const void* post, void* st, cudaStream_t s) {
-        if (c.Q == 9)
-            k_scatter<9, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, (const T*)post, (T*)st);
-        else
-            k_scatter<19, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, (const T*)post, (T*)st);
+    // base subtracted from direction i of N (is_b = false) or B (true) in storage
+    static double storage_base(const StepConfig& c, int i, bool is_b) {
+        if (!PopStore<S>::kShift) return 0.0;
+        return is_b ? 0.5 * c.chi[i] : c.chi[i];
     }
 
-    static void gather(const StepConfig& c, const uint8_t* cls, const void* st, void* post, cudaStream_t s) {
+    static void scatter_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* post_i,
+                            const void* post_opp, void* st, cudaStream_t s) {
+        const T base = (T)storage_base(c, i, is_b);
+        const float scale = is_b ? kScaleB : kScaleN;
         if (c.Q == 9)
-            k_gather<9, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, (const T*)st, (T*)post);
+            k_scatter_dir<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const T*)post_i,
+                                                                   (const T*)post_opp, base, scale, (S*)st);
         else
-            k_gather<19, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, (const T*)st, (T*)post);
+            k_scatter_dir<19, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const T*)post_i,
+                                                                    (const T*)post_opp, base, scale, (S*)st);
+    }
+
+    static void gather_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* st, void* post,
+                           cudaStream_t s) {
+        const T base = (T)storage_base(c, i, is_b);
+        const float scale = is_b ? kScaleB : kScaleN;
+        if (c.Q == 9)
+            k_gather_dir<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const S*)st, base, scale, (T*)post);
+        else
+            k_gather_dir<19, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const S*)st, base, scale, (T*)post);
     }
 
     static int diag_blocks(const Dims& d) {
@@ -147,17 +165,19 @@ struct Launch {
     static void diag(const StepConfig& c, const uint8_t* cls, const void* Nst, const void* phi, const void* u,
                      const void* p, const ProbeDev& pr, double* partial, double* out, cudaStream_t s) {
         const int nb = diag_blocks(c.d);
+        const StepParams<T> P = params(c);
         if (c.Q == 9)
-            k_diag_partial<9, T><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, (const T*)Nst, (const T*)phi,
-                                                             (const T*)u, (const T*)p, pr, partial);
+            k_diag_partial<9, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, P, (const S*)Nst,
+                                                                (const T*)phi, (const T*)u, (const T*)p, pr, partial);
         else
-            k_diag_partial<19, T><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, (const T*)Nst,
-                                                              (const T*)phi, (const T*)u, (const T*)p, pr, partial);
+            k_diag_partial<19, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, P, (const S*)Nst,
+                                                                 (const T*)phi, (const T*)u, (const T*)p, pr, partial);
         k_diag_final<<<1, 32, 0, s>>>(nb, partial, out);
     }
 };
 
-extern template struct Launch<float>;
-extern template struct Launch<double>;
+extern template struct Launch<double, double>;
+extern template struct Launch<float, float>;
+extern template struct Launch<float, __half>;
 
 }  // namespace lbmgpu

@@ -17,7 +17,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOU
     0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_UNSTABLE",
                 -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_UNSUPPORTED"}
-FP64, FP32 = 0, 1
+FP64, FP32, FP16 = 0, 1, 2     # FP16: FP32 arithmetic, FP16 population storage
 GHOST_PRESENT, GHOST_FAKHARI = 0, 1
 FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 

@@ -18,7 +18,11 @@ from paper_2605_30878_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {lbm.FP64: 1e-12, lbm.FP32: 1e-4}
+# FP16 storage keeps 11 significant bits of the stored deviations; a B
+# deviation reaches chi_0/2 ~ 0.46, so one stored value carries up to 2.2e-4 of
+# rounding (2.4e-4 relative to max B) and phi sums 19 of them: 2e-3 leaves room
+# for a few steps of accumulation.
+TOL = {lbm.FP64: 1e-12, lbm.FP32: 1e-4, lbm.FP16: 2e-3}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -71,21 +75,26 @@ def small_3d(theta=60.0, rho_ratio=1000.0, shape=(28, 36, 40), R=7.0, R0=6.0):
     return dict(params=params, solid=solid, ghosts=ghosts, drop_center=tuple(drop), R0=R0)
 
 
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
 def test_state_roundtrip(precision):
     cfg = small_3d()
     g = lbm.Domain(dict(cfg["params"], precision=precision), cfg["solid"], cfg["ghosts"])
     fluid = cfg["solid"].reshape(-1) == 0
-    N, B, u, p = wl.random_state(19, fluid.size, fluid, seed=1)
+    o = oracle.Oracle(cfg["params"], cfg["solid"], cfg["ghosts"])
+    o.init_droplet(cfg["drop_center"], cfg["R0"])
+    chi = o.get("N")[:, np.nonzero(fluid)[0][0]]
+    N, B, u, p = wl.random_state(19, fluid.size, fluid, seed=1, base=chi)     # near the rest state
     phi = np.where(fluid, np.random.default_rng(2).uniform(0, 1, fluid.size), 0.0)
     for f, v in (("N", N), ("B", B), ("u", u), ("p", p), ("phi", phi)):
         g.write(f, v)
         r = g.read(f)
-        tol = 0.0 if precision == lbm.FP64 else 1e-7
-        assert rel(r, v, fluid) <= tol
+        tol = {lbm.FP64: 0.0, lbm.FP32: 1e-7, lbm.FP16: 5e-4}[precision]
+        if precision == lbm.FP16 and f in ("u", "p", "phi"):
+            tol = 1e-7                      # fields stay FP32 in this mode
+        assert rel(r, v, fluid) <= tol, f
 
 
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
 def test_initial_state_matches(precision):
     cfg = wl.cylinder_config()
     g, o = pair(cfg, precision)
@@ -105,7 +114,7 @@ def test_initial_state_matches(precision):
 
 @pytest.mark.parametrize("Q", [9, 19])
 @pytest.mark.parametrize("rho_ratio", [1.0, 1000.0])
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
 def test_one_step_from_a_random_state(Q, rho_ratio, precision):
     """One step from identical seeded non-equilibrium states (every term active)."""
     if Q == 9:
@@ -131,32 +140,68 @@ def test_one_step_from_a_random_state(Q, rho_ratio, precision):
     compare(g, o, cfg["solid"], precision)
 
 
+def _resync_one_step(g, cfg, precision):
+    """Give the oracle the GPU's current state, advance both one step, compare:
+    the step map itself, from identical inputs, at the full tolerance."""
+    o = oracle.Oracle(cfg["params"], cfg["solid"], cfg["ghosts"])
+    for f in ("N", "B", "phi", "u", "p"):
+        o.set(f, g.read(f))
+    g.step(1)
+    o.step(1)
+    compare(g, o, cfg["solid"], precision)
+
+
 @pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
 def test_cylinder_64_parity_over_2000_steps(precision):
     """D2Q9 64x64, cylinder R = 12, drop R0 = 10 tangent on top, theta = 60 deg,
-    density ratio 1, tau = 1: GPU vs oracle after 1, 10, 100 and 2000 steps."""
+    density ratio 1, tau = 1, GPU vs oracle over 2000 steps.
+
+    The spreading of the tangent drop amplifies rounding: on the oracle alone a
+    2e-16 perturbation of the initial populations grows ~500x by step 100.  So at
+    each checkpoint (1, 10, 100, 2000 steps) (a) the trajectories may differ by no
+    more than 1e-12 or 100x the growth of such a 1-ulp perturbation on the oracle
+    itself, and (b) the step map, restarted from the GPU's state on both sides,
+    agrees to the full tolerance."""
     cfg = wl.cylinder_config()
     g, o = pair(cfg, precision)
     g.init_droplet(cfg["drop_center"], cfg["R0"])
     o.init_droplet(cfg["drop_center"], cfg["R0"])
+    ref = oracle.Oracle(cfg["params"], cfg["solid"], cfg["ghosts"])       # 1-ulp perturbed oracle
+    ref.init_droplet(cfg["drop_center"], cfg["R0"])
+    rng = np.random.default_rng(21)
+    for f in ("N", "B"):
+        v = ref.get(f)
+        ref.set(f, v * (1.0 + 2e-16 * rng.uniform(-1, 1, v.shape)))
+    fluid = cfg["solid"].reshape(-1) == 0
+    tol = TOL[precision]
     done = 0
     for target in (1, 10, 100, 2000):
         g.step(target - done)
         o.step(target - done)
+        ref.step(target - done)
         done = target
-        compare(g, o, cfg["solid"], precision)
-    probe_o = oracle.make_probe(1, cfg["solid_center"], cfg["R"], (0, 1, 0), 6.0)
-    probe_g = lbm.make_probe(1, cfg["solid_center"], cfg["R"], (0, 1, 0), 6.0)
-    dg, do = g.diagnostics(probe_g), o.diagnostics(probe_o)
-    tol = 1e-10 if precision == lbm.FP64 else 1e-4
-    for k in ("phi_sum", "pop_sum", "mass_liquid", "mass_gas", "fit_radius", "apex", "p_in", "p_out"):
-        assert abs(dg[k] - do[k]) <= tol * max(1.0, abs(do[k])), k
-    assert abs(dg["max_u"] - do["max_u"]) <= tol * 10 * do["max_u"] + 1e-15
-    assert dg["n_fluid"] == do["n_fluid"] and dg["n_iface"] == do["n_iface"]
-    assert abs(math.degrees(dg["contact_angle"] - do["contact_angle"])) < (1e-6 if precision == lbm.FP64 else 0.5)
+        for f in ("N", "B", "phi"):
+            sens = rel(ref.get(f), o.get(f), fluid)
+            gap = rel(g.read(f), o.get(f), fluid)
+            assert gap <= max(tol, 100.0 * sens), (target, f, gap, sens)
+        if target == 2000:
+            probe_o = oracle.make_probe(1, cfg["solid_center"], cfg["R"], (0, 1, 0), 6.0)
+            probe_g = lbm.make_probe(1, cfg["solid_center"], cfg["R"], (0, 1, 0), 6.0)
+            dg, do = g.diagnostics(probe_g), o.diagnostics(probe_o)
+            dtol = 1e-10 if precision == lbm.FP64 else 1e-4
+            for k in ("phi_sum", "pop_sum", "mass_liquid", "mass_gas", "fit_radius", "apex", "p_in", "p_out"):
+                assert abs(dg[k] - do[k]) <= dtol * max(1.0, abs(do[k])), k
+            assert abs(dg["max_u"] - do["max_u"]) <= dtol * 10 * do["max_u"] + 1e-15
+            assert dg["n_fluid"] == do["n_fluid"] and dg["n_iface"] == do["n_iface"]
+            assert abs(math.degrees(dg["contact_angle"] - do["contact_angle"])) < (1e-6 if precision == lbm.FP64
+                                                                                      else 0.5)
+        _resync_one_step(g, cfg, precision)
+        o.step(1)
+        ref.step(1)
+        done += 1
 
 
-@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
 def test_sphere_3d_parity_ragged_tiles(precision):
     """D3Q19 40x36x28 (ragged against the 32x4x2 tiles), sphere R = 7, drop on its
     pole at theta = 60 deg, density ratio 1000, viscosity ratio 100."""
