@@ -25,6 +25,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -46,6 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_GRID)
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-case batched measurement")
+    ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="population storage: fp32 (the bench default) or fp16 (shifted, scaled)")
     return ap.parse_args()
@@ -215,6 +219,69 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched cases
+
+def batch_cases(seed=2, count=64):
+    """64 independent D3Q19 drop-on-sphere cases: grid n ~ U{48..128}, sphere
+    R = U(0.2, 0.3) n at the centre, drop R0 = 0.75 R at theta ~ U(20, 160) deg,
+    density ratio in {1, 10, 1000} (viscosity ratio 100 at 1000, else 1), FP32."""
+    from paper_2605_30878_gb300 import workloads as wl
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(48, 129))
+        R = float(rng.uniform(0.2, 0.3) * n)
+        theta = float(rng.uniform(20.0, 160.0))
+        ratio = float(rng.choice([1.0, 10.0, 1000.0]))
+        out.append(wl.sphere_config(n=n, R=R, R0=0.75 * R, theta_deg=theta, rho_ratio=ratio,
+                                    mu_ratio=100.0 if ratio == 1000.0 else 1.0, precision=1))
+    return out
+
+
+def run_batch_bench(lbm, steps):
+    """Aggregate MLUPS of the 64 cases advanced by one batched launch per phase
+    (tile shape autotuned) against the same cases each stepped by its own launches."""
+    import torch
+    cfgs = batch_cases()
+    doms = []
+    for c in cfgs:
+        d = lbm.Domain(c["params"], c["solid"], c["ghosts"])
+        d.init_droplet(c["drop_center"], c["R0"])
+        doms.append(d)
+    nodes = sum(int((c["solid"] == 0).sum()) for c in cfgs)      # fluid nodes, as the main metric
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for d in doms:
+        d.step(3)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for d in doms:
+        d.step(steps)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    t_plain = ev[0].elapsed_time(ev[1]) * 1e-3
+    b = lbm.Batch(doms)
+    chosen, trial_ms = b.tune(steps_per_trial=10)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    b.step(steps)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    t_batch = ev[2].elapsed_time(ev[3]) * 1e-3
+    b.sync()
+    res = {"cases": len(cfgs), "nodes": nodes, "steps": steps,
+           "mlups_batched": nodes * steps / t_batch / 1e6, "mlups_plain": nodes * steps / t_plain / 1e6,
+           "speedup": t_plain / t_batch, "tile_shape_chosen": int(chosen),
+           "tune_ms_per_step": [round(float(x), 4) for x in trial_ms],
+           "launches_per_step_batched": b.launches_per_step(),
+           "launches_per_step_plain": sum(d.launches_per_step() for d in doms)}
+    b.close()
+    for d in doms:
+        d.close()
+    torch.cuda.empty_cache()
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -326,6 +393,10 @@ def run_ours(args):
             cpu = {"value": rate, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
                    "sample": "%d FP64 oracle steps of the %d^3 workload after 1 warm-up step (%.1f s)" % (st, n, dt)}
 
+        batched = None
+        if world == 1 and not args.no_batch:
+            batched = run_batch_bench(lbm, args.batch_steps)
+
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -352,6 +423,7 @@ def run_ours(args):
             "gpu_launches": launches * args.steps,
             "clocks": clk,
             "contact_angle": angle,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

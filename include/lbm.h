@@ -234,6 +234,48 @@ lbm_status lbm_phase_sums_noalloc(const uint8_t* dev_class, const void* dev_phi,
                                   int64_t plane, double rho_l, double rho_g, double* dev_out,
                                   void* cuda_stream, char* err, size_t err_len);
 
+/* ---- Batches: several domains advanced together (no counterpart in the
+ * paper, which runs one case at a time).  A batch advances domains of the same
+ * lattice and precision with one launch per phase (ghost update; step, split
+ * into domains with and without density contrast; color), one block per tile
+ * of a flat list of the tiles of every domain, replayed from CUDA graphs.
+ * Each domain keeps its own state, parameters and error flag;
+ * results are bitwise identical to stepping each domain alone.  While a
+ * domain belongs to a batch it must only be stepped through the batch
+ * (lbm_batch_step reports LBM_ERR_ARG otherwise); reading its state and
+ * diagnostics stay available. */
+typedef struct lbm_batch lbm_batch;
+
+/* Build a batch over doms[0..n-1] (not owned; they must outlive the batch).
+ * Launches go to cuda_stream (NULL = default stream).  Errors: LBM_ERR_ARG
+ * (mixed lattice/precision, repeated domain), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_stream, lbm_batch** out);
+
+/* Advance every domain of the batch n >= 0 steps, asynchronously. */
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n);
+
+/* Wait for the batch stream; LBM_ERR_UNSTABLE if any domain went non-finite. */
+lbm_status lbm_batch_sync(lbm_batch* b);
+
+/* Autotuner: time steps_per_trial batched steps with each of the three block
+ * tile shapes (D3Q19: 32x4x2, 32x2x4, 32x8x1; D2Q9: 32x8, 64x4, 128x2), keep the
+ * fastest; ms_per_step[3] (may be NULL) receives the timings.  Tuning advances
+ * every domain by 3 (steps_per_trial + 1) steps and synchronises. */
+lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_trial, int32_t* chosen, double* ms_per_step);
+
+/* Current tile shape of the batch, or set one directly (0, 1, 2). */
+int32_t lbm_batch_variant(const lbm_batch* b);
+lbm_status lbm_batch_set_variant(lbm_batch* b, int32_t variant);
+
+/* Kernel launches one batched step makes: ghost update (when any domain has
+ * ghost nodes), step kernel once per contrast class present, color kernel. */
+int32_t lbm_batch_launches_per_step(const lbm_batch* b);
+
+/* Message of the last failed call on b (of the last failed create if b is NULL). */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+void lbm_batch_destroy(lbm_batch* b);
+
 /* Message of the last failed call on dom, or of the last failed
  * lbm_create_domain when dom is NULL. */
 const char* lbm_last_error(const lbm_domain* dom);

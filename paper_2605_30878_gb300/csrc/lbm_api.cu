@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -783,6 +785,326 @@ void lbm_destroy(lbm_domain* d) {
     if (d->cap) cudaStreamDestroy(d->cap);
     if (d->own_ws && d->ws) cudaFree(d->ws);
     delete d;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many domains advanced by one launch per phase.
+// ===========================================================================
+struct lbm_batch {
+    std::vector<lbm_domain*> doms;
+    int Q = 0, precision = 0, GK = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    std::vector<int> cur0;             // each domain's buffer parity when the batch was made
+    int parity = 0;                    // steps taken by the batch, mod 2
+    int variant = 0;
+    int ntiles[kTileVariants] = {0, 0, 0};
+    int ncontrast[kTileVariants] = {0, 0, 0};   // tiles of domains with density contrast come first
+    int device = 0;
+    int slot0 = -1;                    // first of doms.size() slots of the constant table
+    char* dev = nullptr;               // one allocation for every device table
+    int4* tiles[kTileVariants] = {nullptr, nullptr, nullptr};   // {slot, x0, y0, z0}
+    void* ghost_tabs = nullptr;
+    int64_t* ghost_begin = nullptr;
+    int64_t total_ghosts = 0;
+    cudaGraphExec_t g1[2] = {nullptr, nullptr};
+    cudaGraphExec_t g8 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_error;
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& m) {
+    if (b) b->err = m; else g_batch_error = m;
+    return s;
+}
+
+// Slots of the constant tables (one table per precision and GPU), handed out
+// as contiguous ranges, first fit.
+std::mutex g_slot_mutex;
+std::map<std::pair<int, int>, std::vector<char>> g_slots_used;
+
+int reserve_slots(int device, int precision, int n) {
+    std::lock_guard<std::mutex> lk(g_slot_mutex);
+    std::vector<char>& used = g_slots_used[{device, precision}];
+    used.resize(kBatchSlots, 0);
+    for (int s0 = 0; s0 + n <= kBatchSlots; ++s0) {
+        int k = 0;
+        while (k < n && !used[s0 + k]) ++k;
+        if (k == n) {
+            for (k = 0; k < n; ++k) used[s0 + k] = 1;
+            return s0;
+        }
+        s0 += k;
+    }
+    return -1;
+}
+
+void release_slots(int device, int precision, int s0, int n) {
+    std::lock_guard<std::mutex> lk(g_slot_mutex);
+    std::vector<char>& used = g_slots_used[{device, precision}];
+    for (int k = 0; k < n && s0 + k < (int)used.size(); ++k) used[s0 + k] = 0;
+}
+
+template <typename F>
+void bdispatch(int precision, F&& f) {
+    switch (precision) {
+    case LBM_FP64: f(Launch<double, double>{}); break;
+    case LBM_FP32: f(Launch<float, float>{}); break;
+    default: f(Launch<float, __half>{}); break;
+    }
+}
+
+// Appends the tiles {slot, x0, y0, z0} of a domain for tile shape V (the
+// shapes of Tile<Q, V>).
+void append_tiles(int Q, int V, const lbm_params& P, int i, std::vector<int4>& out) {
+    int TX, TY, TZ;
+    if (Q == 9) { TX = V == 0 ? 32 : (V == 1 ? 64 : 128); TY = V == 0 ? 8 : (V == 1 ? 4 : 2); TZ = 1; }
+    else { TX = 32; TY = V == 0 ? 4 : (V == 1 ? 2 : 8); TZ = V == 0 ? 2 : (V == 1 ? 4 : 1); }
+    for (int z = 0; z < P.nz; z += TZ)
+        for (int y = 0; y < P.ny; y += TY)
+            for (int x = 0; x < P.nx; x += TX) out.push_back(make_int4(i, x, y, z));
+}
+
+void batch_launch_step(lbm_batch* b, int parity, cudaStream_t s) {
+    const int V = b->variant;
+    bdispatch(b->precision, [&](auto Lx) {
+        using L = decltype(Lx);
+        L::ghost_batched(b->GK, b->ghost_tabs, b->ghost_begin, (int)b->doms.size(), b->total_ghosts, s);
+        L::step_phi_batched(b->Q, V, b->tiles[V], b->ntiles[V], b->ncontrast[V], parity, s);
+    });
+}
+
+lbm_status batch_capture(lbm_batch* b) {
+    for (auto* g : {&b->g1[0], &b->g1[1], &b->g8})
+        if (*g) { cudaGraphExecDestroy(*g); *g = nullptr; }
+    for (int k = 0; k < 3; ++k) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, cudaGetErrorString(e));
+        if (k < 2) batch_launch_step(b, k, b->cap);
+        else for (int t = 0; t < 8; ++t) batch_launch_step(b, t & 1, b->cap);
+        e = cudaStreamEndCapture(b->cap, &g);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t* dst = k == 0 ? &b->g1[0] : (k == 1 ? &b->g1[1] : &b->g8);
+        e = cudaGraphInstantiate(dst, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_stream, lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!doms || n < 1) return bfail(nullptr, LBM_ERR_ARG, "a batch needs at least one domain");
+    lbm_batch* b = new lbm_batch();
+    b->Q = doms[0]->prm.lattice;
+    b->precision = doms[0]->prm.precision;
+    b->GK = doms[0]->lay.GK;
+    for (int i = 0; i < n; ++i) {
+        if (!doms[i]) { delete b; return bfail(nullptr, LBM_ERR_ARG, "NULL domain in the batch"); }
+        if (doms[i]->prm.lattice != b->Q || doms[i]->prm.precision != b->precision) {
+            delete b;
+            return bfail(nullptr, LBM_ERR_ARG, "all domains of a batch need the same lattice and precision");
+        }
+        for (int j = 0; j < i; ++j)
+            if (doms[j] == doms[i]) { delete b; return bfail(nullptr, LBM_ERR_ARG, "a domain appears twice"); }
+        b->doms.push_back(doms[i]);
+        b->cur0.push_back(doms[i]->cur);
+    }
+    b->stream = (cudaStream_t)cuda_stream;
+    if (n > kBatchSlots) {
+        delete b;
+        return bfail(nullptr, LBM_ERR_ARG, "a batch holds at most " + std::to_string(kBatchSlots) + " domains");
+    }
+    cudaGetDevice(&b->device);
+    b->slot0 = reserve_slots(b->device, b->precision, n);
+    if (b->slot0 < 0) {
+        delete b;
+        return bfail(nullptr, LBM_ERR_OOM, "no " + std::to_string(n) + " free slots left in the constant table (" +
+                                               std::to_string(kBatchSlots) + " per precision, shared by live batches)");
+    }
+    // host copies of the tables
+    size_t esz = 0, gsz = 0;
+    bdispatch(b->precision, [&](auto Lx) {
+        using L = decltype(Lx);
+        esz = L::entry_size(); gsz = L::ghost_table_size();
+    });
+    std::vector<char> he(esz * n), hg(gsz * n);
+    std::vector<int64_t> gbegin(n + 1, 0);
+    std::vector<std::vector<int4>> tiles(kTileVariants);
+    for (int i = 0; i < n; ++i) {
+        lbm_domain* d = b->doms[i];
+        const Layout& L = d->lay;
+        bdispatch(b->precision, [&](auto Lx) {
+            using LL = decltype(Lx);
+            StepPtrs sp[2];
+            for (int k = 0; k < 2; ++k) {
+                const int c = b->cur0[i] ^ k;
+                sp[k].Nin = d->N(c); sp[k].Bin = d->B(c); sp[k].Nout = d->N(1 - c); sp[k].Bout = d->B(1 - c);
+                sp[k].phi = d->phi(); sp[k].u_in = d->U(c); sp[k].u_out = d->U(1 - c); sp[k].p = d->p();
+                sp[k].mask = d->mask(); sp[k].err = d->errflag();
+            }
+            LL::fill_entry(&he[esz * i], d->cfg, sp);
+            LL::fill_ghost_table(&hg[gsz * i], d->ng, d->at<int32_t>(L.off_gnode), d->at<int32_t>(L.off_gcorner),
+                                 d->at<void>(L.off_gwt), d->cfg.exp_eps, d->cfg.eps, d->phi(), d->cfg.ghost_rule);
+        });
+        gbegin[i + 1] = gbegin[i] + d->ng;
+    }
+    // tiles of the domains with density contrast first, then the others
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < n; ++i) {
+            if (b->doms[i]->contrast != (pass == 0)) continue;
+            for (int V = 0; V < kTileVariants; ++V) {
+                append_tiles(b->Q, V, b->doms[i]->prm, b->slot0 + i, tiles[V]);
+                if (pass == 0) b->ncontrast[V] = (int)tiles[V].size();
+            }
+        }
+    b->total_ghosts = gbegin[n];
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t r = off; off = round_up(off + bytes, 256); return r; };
+    const size_t o_g = take(hg.size()), o_gb = take(gbegin.size() * 8);
+    size_t o_t[kTileVariants];
+    for (int V = 0; V < kTileVariants; ++V) {
+        if (tiles[V].size() > (size_t)INT32_MAX) {
+            lbm_batch_destroy(b);
+            return bfail(nullptr, LBM_ERR_ARG, "too many tiles");
+        }
+        o_t[V] = take(tiles[V].size() * sizeof(int4));
+    }
+    if (cudaMalloc((void**)&b->dev, off) != cudaSuccess) {
+        cudaGetLastError();
+        lbm_batch_destroy(b);
+        return bfail(nullptr, LBM_ERR_OOM, "cudaMalloc of the batch tables failed");
+    }
+    b->ghost_tabs = b->dev + o_g;
+    b->ghost_begin = (int64_t*)(b->dev + o_gb);
+    cudaError_t e = cudaSuccess;
+    bdispatch(b->precision, [&](auto Lx) { e = decltype(Lx)::upload_entries(b->slot0, he.data(), n); });
+    if (e == cudaSuccess) e = cudaMemcpy(b->ghost_tabs, hg.data(), hg.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->ghost_begin, gbegin.data(), gbegin.size() * 8, cudaMemcpyHostToDevice);
+    for (int V = 0; V < kTileVariants && e == cudaSuccess; ++V) {
+        b->tiles[V] = (int4*)(b->dev + o_t[V]);
+        b->ntiles[V] = (int)tiles[V].size();
+        e = cudaMemcpy(b->tiles[V], tiles[V].data(), tiles[V].size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        std::string m = cudaGetErrorString(e);
+        lbm_batch_destroy(b);
+        return bfail(nullptr, LBM_ERR_CUDA, "batch set-up: " + m);
+    }
+    lbm_status st = batch_capture(b);
+    if (st != LBM_OK) {
+        std::string m = b->err;
+        lbm_batch_destroy(b);
+        return bfail(nullptr, st, m);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
+    if (!b) return bfail(b, LBM_ERR_ARG, "NULL batch");
+    if (n < 0) return bfail(b, LBM_ERR_ARG, "n must be >= 0");
+    for (size_t i = 0; i < b->doms.size(); ++i)
+        if (b->doms[i]->cur != (b->cur0[i] ^ b->parity))
+            return bfail(b, LBM_ERR_ARG, "domain " + std::to_string(i) + " was stepped outside the batch; recreate it");
+    int64_t left = n;
+    while (left > 0) {
+        cudaError_t e;
+        if (b->parity == 0 && left >= 8) { e = cudaGraphLaunch(b->g8, b->stream); left -= 8; }
+        else { e = cudaGraphLaunch(b->g1[b->parity], b->stream); b->parity ^= 1; left -= 1; }
+        if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    for (auto* d : b->doms) {
+        d->step += n;
+        if (n & 1) d->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+    if (!b) return bfail(b, LBM_ERR_ARG, "NULL batch");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, cudaGetErrorString(e));
+    for (size_t i = 0; i < b->doms.size(); ++i) {
+        lbm_status st = check_err_flag(b->doms[i]);
+        if (st != LBM_OK) return bfail(b, st, "domain " + std::to_string(i) + ": " + b->doms[i]->err);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_trial, int32_t* chosen, double* ms_per_step) {
+    if (!b || steps_per_trial < 1) return bfail(b, LBM_ERR_ARG, "bad arguments");
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, LBM_ERR_CUDA, "cudaEventCreate failed");
+    double best = 1e300;
+    int best_v = 0;
+    for (int V = 0; V < kTileVariants; ++V) {
+        b->variant = V;
+        batch_launch_step(b, b->parity, b->stream);        // warm-up step of this shape
+        b->parity ^= 1;
+        cudaEventRecord(e0, b->stream);
+        for (int t = 0; t < steps_per_trial; ++t) {
+            batch_launch_step(b, b->parity, b->stream);
+            b->parity ^= 1;
+        }
+        cudaEventRecord(e1, b->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return bfail(b, LBM_ERR_CUDA, cudaGetErrorString(e)); }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / steps_per_trial;
+        if (ms_per_step) ms_per_step[V] = per;
+        if (per < best) { best = per; best_v = V; }
+        const int64_t taken = steps_per_trial + 1;
+        for (auto* d : b->doms) { d->step += taken; if (taken & 1) d->cur ^= 1; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->variant = best_v;
+    if (chosen) *chosen = best_v;
+    return batch_capture(b);
+}
+
+int32_t lbm_batch_variant(const lbm_batch* b) { return b ? b->variant : -1; }
+
+lbm_status lbm_batch_set_variant(lbm_batch* b, int32_t v) {
+    if (!b || v < 0 || v >= kTileVariants) return bfail(b, LBM_ERR_ARG, "variant must be 0, 1 or 2");
+    b->variant = v;
+    return batch_capture(b);
+}
+
+int32_t lbm_batch_launches_per_step(const lbm_batch* b) {
+    if (!b) return -1;
+    const int V = b->variant;
+    return (b->total_ghosts > 0) + (b->ncontrast[V] > 0) + (b->ntiles[V] > b->ncontrast[V]) + 1;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    // the slots may be handed to another batch: let this batch's launches finish first
+    if (b->slot0 >= 0) {
+        cudaStreamSynchronize(b->stream);
+        release_slots(b->device, b->precision, b->slot0, (int)b->doms.size());
+    }
+    for (auto* g : {b->g1[0], b->g1[1], b->g8})
+        if (g) cudaGraphExecDestroy(g);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->dev) cudaFree(b->dev);
+    delete b;
 }
 
 }  // extern "C"

@@ -1,5 +1,5 @@
 // FP32 arithmetic and storage: instantiation of every kernel launcher.
-#include "lbm_launch.cuh"
+#include "lbm_launch_impl.cuh"
 
 namespace lbmgpu {
 template struct Launch<float, float>;

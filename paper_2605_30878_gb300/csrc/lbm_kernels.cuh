@@ -130,12 +130,15 @@ struct StepBuffers {
 // so the pull in direction i bounces back; MASK_NOT_FLUID marks non-fluid x.
 constexpr uint32_t MASK_NOT_FLUID = 0x80000000u;
 
-template <int Q>
+// Block tile of the step kernels: 256 threads, one node each, in one of three
+// shapes (V = 0, 1, 2) that the batch autotuner chooses between.
+//   D3Q19: 32x4x2, 32x2x4, 32x8x1      D2Q9: 32x8, 64x4, 128x2
+template <int Q, int V = 0>
 struct Tile {
     static constexpr int D = Lattice<Q>::D;
-    static constexpr int TX = 32;
-    static constexpr int TY = (D == 2) ? 8 : 4;
-    static constexpr int TZ = (D == 2) ? 1 : 2;
+    static constexpr int TX = (D == 2) ? (V == 0 ? 32 : (V == 1 ? 64 : 128)) : 32;
+    static constexpr int TY = (D == 2) ? (V == 0 ? 8 : (V == 1 ? 4 : 2)) : (V == 0 ? 4 : (V == 1 ? 2 : 8));
+    static constexpr int TZ = (D == 2) ? 1 : (V == 0 ? 2 : (V == 1 ? 4 : 1));
     static constexpr int HX = TX + 2;
     static constexpr int HY = TY + 2;
     static constexpr int HZ = (D == 2) ? 1 : TZ + 2;
@@ -144,6 +147,7 @@ struct Tile {
     // offset of the halo slot of x + c in a halo tile
     __host__ __device__ static constexpr int off(int cx, int cy, int cz) { return cx + HX * (cy + HY * cz); }
 };
+constexpr int kTileVariants = 3;
 
 __device__ __forceinline__ int wrap_any(int v, int n) {
     v %= n;
@@ -179,12 +183,12 @@ struct Wrap {
 // Load a block's color (and optionally velocity) tile with a one-node halo.
 // Ghost nodes hold their fresh ghost color; the velocity at solid nodes is 0
 // in memory (never written), so no node class is needed here.
-template <int Q, typename T, bool LOAD_U>
+template <int Q, int V, typename T, bool LOAD_U>
 __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __restrict__ phi,
                                           const T* __restrict__ u, T* s_phi, T* s_u, int x0, int y0, int z0) {
     // one warp per halo row (fixed hy, hz): the row's periodic y/z image is
     // computed once, lanes walk the row's HX consecutive x positions
-    using Tl = Tile<Q>;
+    using Tl = Tile<Q, V>;
     constexpr int D = Tl::D;
     constexpr int ROWS = Tl::HY * Tl::HZ;
     constexpr int WARPS = Tl::THREADS / 32;
@@ -212,13 +216,9 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __res
 // k_phi: Eq. (phiUpdate) on pulled B*
 // ---------------------------------------------------------------------------
 template <int Q, typename T, typename S>
-__global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const S* __restrict__ Bst,
-                                                          const uint32_t* __restrict__ mask, T* __restrict__ phi) {
+__device__ __forceinline__ void phi_node(const StepParams<T>& P, const S* __restrict__ Bst,
+                                         const uint32_t* __restrict__ mask, T* __restrict__ phi, int x, int y, int z) {
     using L = Lattice<Q>;
-    using Tl = Tile<Q>;
-    const int x = blockIdx.x * Tl::TX + threadIdx.x;
-    const int y = blockIdx.y * Tl::TY + threadIdx.y;
-    const int z = blockIdx.z * Tl::TZ + threadIdx.z;
     if (x >= P.nx || y >= P.ny || z >= P.nz) return;
     const int node = x + P.nx * (y + P.ny * z);
     const uint32_t m = __ldg(mask + node);
@@ -235,7 +235,15 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const
         s += (T)PS::load_moving(mv, idx, kScaleB);
     }
     // stored deviations B_i - chi_i/2 sum to phi - 1/2
-    phi[node] = PopStore<S>::kShift ? T(0.5) + s : s;
+    phi[node] = PS::kShift ? T(0.5) + s : s;
+}
+
+template <int Q, typename T, typename S>
+__global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const S* __restrict__ Bst,
+                                                          const uint32_t* __restrict__ mask, T* __restrict__ phi) {
+    using Tl = Tile<Q>;
+    phi_node<Q, T, S>(P, Bst, mask, phi, blockIdx.x * Tl::TX + threadIdx.x, blockIdx.y * Tl::TY + threadIdx.y,
+                      blockIdx.z * Tl::TZ + threadIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -385,17 +393,13 @@ __device__ __forceinline__ void node_update_literal(const StepParams<double>& P,
     }
 }
 
-template <int Q, typename T, typename S, bool CONTRAST>
-__global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, StepBuffers<T, S> b) {
+// One fluid node of the step, reading the block's halo tile (already loaded).
+template <int Q, int V, typename T, typename S, bool CONTRAST>
+__device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuffers<T, S>& b,
+                                          const T* __restrict__ s_phi, const T* __restrict__ s_u, int x, int y, int z) {
     using L = Lattice<Q>;
-    using Tl = Tile<Q>;
+    using Tl = Tile<Q, V>;
     constexpr int D = L::D;
-    __shared__ T s_phi[Tl::HN];
-    __shared__ T s_u[CONTRAST ? D * Tl::HN : 1];
-    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
-    load_halo<Q, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
-    __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     if (x >= P.nx || y >= P.ny || z >= P.nz) return;
     const int node = x + P.nx * (y + P.ny * z);
     const uint32_t m = __ldg(b.mask + node);
@@ -649,6 +653,104 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_step(StepParams<T> P, Step
     b.p[node] = p;
     if (!(uu < T(1e30))) atomicOr(b.err, 1);   // also catches NaN
     }
+}
+
+// Halo load, barrier, then every thread's node of the tile at (x0, y0, z0).
+template <int Q, int V, typename T, typename S, bool CONTRAST>
+__device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuffers<T, S>& b, T* s_phi, T* s_u,
+                                          int x0, int y0, int z0) {
+    load_halo<Q, V, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
+    __syncthreads();
+    step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, x0 + threadIdx.x, y0 + threadIdx.y, z0 + threadIdx.z);
+}
+
+template <int Q, typename T, typename S, bool CONTRAST, int V = 0>
+__global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_step(StepParams<T> P, StepBuffers<T, S> b) {
+    using Tl = Tile<Q, V>;
+    __shared__ T s_phi[Tl::HN];
+    __shared__ T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
+    step_tile<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, blockIdx.x * Tl::TX, blockIdx.y * Tl::TY, blockIdx.z * Tl::TZ);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches: every domain of a batch in one launch per phase (two for
+// the step kernel: domains with and without density contrast), one block per
+// tile.  Tiles of all domains form one flat list of {slot, x0, y0, z0}.  Each
+// domain's parameters and buffers sit in one slot of a constant-memory table;
+// b[k] are the buffers for the k-th step parity of the launch.  A block reads
+// its slot at a block-uniform index, so the parameters are constant-cache
+// operands as kernel parameters are in the single-domain kernels.  Every tile
+// is computed by the same step_tile as in the single-domain kernels, so
+// results are bitwise identical.
+// ---------------------------------------------------------------------------
+constexpr int kBatchSlots = 96;        // domains of all live batches of one precision on one GPU
+
+template <typename T, typename S>
+struct BatchEntry {
+    StepParams<T> P;
+    StepBuffers<T, S> b[2];
+};
+
+template <typename T, typename S>
+__constant__ BatchEntry<T, S> c_batch[kBatchSlots];
+
+template <int Q, typename T, typename S, int V, bool CONTRAST>
+__global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_step_batched(const int4* __restrict__ tiles, int parity) {
+    using Tl = Tile<Q, V>;
+    __shared__ T s_phi[Tl::HN];
+    __shared__ T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
+    const int4 t = __ldg(tiles + blockIdx.x);          // {slot, x0, y0, z0}
+    const BatchEntry<T, S>& e = c_batch<T, S>[t.x];
+    step_tile<Q, V, T, S, CONTRAST>(e.P, e.b[parity], s_phi, s_u, t.y, t.z, t.w);
+}
+
+template <int Q, typename T, typename S, int V>
+__global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_phi_batched(const int4* __restrict__ tiles, int parity) {
+    const int4 t = __ldg(tiles + blockIdx.x);
+    const BatchEntry<T, S>& e = c_batch<T, S>[t.x];
+    // this step's output B* is the buffer the step kernel wrote
+    phi_node<Q, T, S>(e.P, e.b[parity].Bout, e.b[parity].mask, e.b[parity].phi, t.y + threadIdx.x, t.z + threadIdx.y,
+                      t.w + threadIdx.z);
+}
+
+// Ghost tables of all domains: ghost g of the batch belongs to the domain d with
+// ghost_begin[d] <= g < ghost_begin[d + 1].
+template <typename T>
+struct GhostTable {
+    int64_t n;
+    const int32_t* node;
+    const int32_t* corner;
+    const T* wt;
+    T exp_eps, eps;
+    T* phi;
+    int rule;
+};
+
+template <int GK, typename T>
+__global__ void __launch_bounds__(256) k_ghost_batched(const GhostTable<T>* __restrict__ tabs,
+                                                       const int64_t* __restrict__ ghost_begin, int ndom,
+                                                       int64_t total) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo = 0, hi = ndom - 1;                     // last d with ghost_begin[d] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ghost_begin[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const GhostTable<T>& t = tabs[lo];
+    const int64_t k = g - ghost_begin[lo];
+    const int64_t n = t.n;
+    T phiF = T(0);
+#pragma unroll
+    for (int c = 0; c < GK; ++c) phiF += t.wt[c * n + k] * t.phi[t.corner[c * n + k]];
+    T phiG;
+    if (t.rule == 0) {
+        phiG = phiF / (phiF + (T(1) - phiF) * t.exp_eps);
+    } else {
+        const T a = T(1) + T(0.5) * t.eps;
+        phiG = T(4) * phiF / (a + sqrt(a * a - T(2) * t.eps * phiF)) - phiF;
+    }
+    t.phi[t.node[k]] = phiG;
 }
 
 }  // namespace lbmgpu

@@ -1,0 +1,227 @@
+// Definitions of the typed kernel launchers declared in lbm_launch.cuh.
+// Included only by the per-precision translation units, which instantiate
+// Launch<T, S> (and so every kernel) once each.
+#pragma once
+
+#include "lbm_launch.cuh"
+
+namespace lbmgpu {
+
+template <typename T, typename S>
+StepParams<T> Launch<T, S>::params(const StepConfig& c) {
+    StepParams<T> P;
+    P.nx = c.d.nx; P.ny = c.d.ny; P.nz = c.d.nz;
+    P.plane = c.d.plane;
+    P.rho_l = (T)c.rho_l; P.rho_g = (T)c.rho_g; P.drho = (T)(c.rho_l - c.rho_g);
+    P.inv_nu_l = (T)(1.0 / c.nu_l); P.inv_nu_g = (T)(1.0 / c.nu_g);
+    P.sigma = (T)c.sigma;
+    P.W = (T)c.W;
+    P.nu_l = (T)c.nu_l; P.nu_g = (T)c.nu_g;
+    P.k48W = (T)(48.0 / c.W); P.k3W2 = (T)(1.5 * c.W); P.two_over_W = (T)(2.0 / c.W);
+    for (int a = 0; a < 3; ++a) P.g[a] = (T)c.g[a];
+    for (int i = 0; i < 19; ++i) P.chi[i] = (T)c.chi[i];
+    P.c2chi = (T)c.c2chi;
+    P.exp_eps = (T)c.exp_eps;
+    return P;
+}
+
+template <typename T, typename S>
+template <int Q>
+dim3 Launch<T, S>::step_grid(const Dims& d) {
+    using Tl = Tile<Q>;
+    return dim3((d.nx + Tl::TX - 1) / Tl::TX, (d.ny + Tl::TY - 1) / Tl::TY, (d.nz + Tl::TZ - 1) / Tl::TZ);
+}
+
+template <typename T, typename S>
+template <int Q>
+dim3 Launch<T, S>::step_block() {
+    using Tl = Tile<Q>;
+    return dim3(Tl::TX, Tl::TY, Tl::TZ);
+}
+
+template <typename T, typename S>
+template <int Q>
+void Launch<T, S>::step_q(const StepConfig& c, const StepPtrs& p, cudaStream_t s) {
+    const StepParams<T> P = params(c);
+    StepBuffers<T, S> b;
+    b.Nin = (const S*)p.Nin; b.Bin = (const S*)p.Bin; b.Nout = (S*)p.Nout; b.Bout = (S*)p.Bout;
+    b.phi = (T*)p.phi; b.u_in = (const T*)p.u_in; b.u_out = (T*)p.u_out; b.p = (T*)p.p;
+    b.mask = p.mask; b.err = p.err;
+    if (c.contrast)
+        k_step<Q, T, S, true><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
+    else
+        k_step<Q, T, S, false><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
+}
+
+template <typename T, typename S>
+void Launch<T, S>::step(const StepConfig& c, const StepPtrs& p, cudaStream_t s) {
+    if (c.Q == 9) step_q<9>(c, p, s); else step_q<19>(c, p, s);
+}
+
+template <typename T, typename S>
+void Launch<T, S>::phi(const StepConfig& c, const void* Bst, const uint32_t* mask, void* phi, cudaStream_t s) {
+    const StepParams<T> P = params(c);
+    if (c.Q == 9)
+        k_phi<9, T, S><<<step_grid<9>(c.d), step_block<9>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi);
+    else
+        k_phi<19, T, S><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi);
+}
+
+template <typename T, typename S>
+void Launch<T, S>::ghost(int GK, int rule, int64_t ng, const int32_t* node, const int32_t* corner, const void* wt,
+                  double exp_eps, double eps, void* phi, cudaStream_t s) {
+    if (ng == 0) return;
+    const unsigned blocks = (unsigned)((ng + 255) / 256);
+    const T* w = (const T*)wt;
+    if (GK == 4 && rule == 0) k_ghost<4, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+    if (GK == 4 && rule == 1) k_ghost<4, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+    if (GK == 8 && rule == 0) k_ghost<8, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+    if (GK == 8 && rule == 1) k_ghost<8, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+}
+
+template <typename T, typename S>
+unsigned Launch<T, S>::flat_blocks(const Dims& d) {
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    int64_t b = (nn + 255) / 256;
+    return (unsigned)(b > 8192 ? 8192 : (b < 1 ? 1 : b));
+}
+
+template <typename T, typename S>
+void Launch<T, S>::init_phi(const StepConfig& c, const uint8_t* cls, void* phi, int mode, const double ctr[3], double R0,
+                     double ghost_value, cudaStream_t s) {
+    if (c.Q == 9)
+        k_init_phi<2, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, (T*)phi, mode, ctr[0], ctr[1], ctr[2], R0, c.W,
+                                                          ghost_value);
+    else
+        k_init_phi<3, T><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, (T*)phi, mode, ctr[0], ctr[1], ctr[2], R0, c.W,
+                                                          ghost_value);
+}
+
+template <typename T, typename S>
+void Launch<T, S>::init_pops(const StepConfig& c, const uint8_t* cls, const void* phi, void* N, void* B, cudaStream_t s) {
+    const StepParams<T> P = params(c);
+    if (c.Q == 9)
+        k_init_pops<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, P, cls, (const T*)phi, (S*)N, (S*)B);
+    else
+        k_init_pops<19, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, P, cls, (const T*)phi, (S*)N, (S*)B);
+}
+
+// base subtracted from direction i of N (is_b = false) or B (true) in storage
+template <typename T, typename S>
+double Launch<T, S>::storage_base(const StepConfig& c, int i, bool is_b) {
+    if (!PopStore<S>::kShift) return 0.0;
+    return is_b ? 0.5 * c.chi[i] : c.chi[i];
+}
+
+template <typename T, typename S>
+void Launch<T, S>::scatter_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* post_i,
+                        const void* post_opp, void* st, cudaStream_t s) {
+    const T base = (T)storage_base(c, i, is_b);
+    const float scale = is_b ? kScaleB : kScaleN;
+    if (c.Q == 9)
+        k_scatter_dir<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const T*)post_i,
+                                                               (const T*)post_opp, base, scale, (S*)st);
+    else
+        k_scatter_dir<19, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const T*)post_i,
+                                                                (const T*)post_opp, base, scale, (S*)st);
+}
+
+template <typename T, typename S>
+void Launch<T, S>::gather_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* st, void* post,
+                       cudaStream_t s) {
+    const T base = (T)storage_base(c, i, is_b);
+    const float scale = is_b ? kScaleB : kScaleN;
+    if (c.Q == 9)
+        k_gather_dir<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const S*)st, base, scale, (T*)post);
+    else
+        k_gather_dir<19, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const S*)st, base, scale, (T*)post);
+}
+
+// ---- batched launches (one block per tile of a flat tile list)
+template <typename T, typename S>
+template <int Qc, int V>
+void Launch<T, S>::step_batched_v(const int4* tiles, int ntiles, int ncontrast, int parity, cudaStream_t s) {
+    using Tl = Tile<Qc, V>;
+    const dim3 block(Tl::TX, Tl::TY, Tl::TZ);     // the tile shape, as in the single-domain kernels
+    if (ncontrast > 0)
+        k_step_batched<Qc, T, S, V, true><<<ncontrast, block, 0, s>>>(tiles, parity);
+    if (ntiles > ncontrast)
+        k_step_batched<Qc, T, S, V, false><<<ntiles - ncontrast, block, 0, s>>>(tiles + ncontrast, parity);
+    k_phi_batched<Qc, T, S, V><<<ntiles, block, 0, s>>>(tiles, parity);
+}
+
+// step kernels then color kernel of every domain (the ghost update precedes them);
+// tiles[0, ncontrast) belong to domains with density contrast
+template <typename T, typename S>
+void Launch<T, S>::step_phi_batched(int Q, int V, const int4* tiles, int ntiles, int ncontrast, int parity,
+                             cudaStream_t s) {
+    if (ntiles == 0) return;
+    if (Q == 9) {
+        if (V == 0) step_batched_v<9, 0>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 1) step_batched_v<9, 1>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 2) step_batched_v<9, 2>(tiles, ntiles, ncontrast, parity, s);
+    } else {
+        if (V == 0) step_batched_v<19, 0>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 1) step_batched_v<19, 1>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 2) step_batched_v<19, 2>(tiles, ntiles, ncontrast, parity, s);
+    }
+}
+
+template <typename T, typename S>
+void Launch<T, S>::fill_entry(void* out, const StepConfig& c, const StepPtrs p[2]) {
+    BatchEntry<T, S> e;
+    e.P = params(c);
+    for (int k = 0; k < 2; ++k) {
+        StepBuffers<T, S>& b = e.b[k];
+        b.Nin = (const S*)p[k].Nin; b.Bin = (const S*)p[k].Bin; b.Nout = (S*)p[k].Nout; b.Bout = (S*)p[k].Bout;
+        b.phi = (T*)p[k].phi; b.u_in = (const T*)p[k].u_in; b.u_out = (T*)p[k].u_out; b.p = (T*)p[k].p;
+        b.mask = p[k].mask; b.err = p[k].err;
+    }
+    std::memcpy(out, &e, sizeof(e));
+}
+
+template <typename T, typename S>
+cudaError_t Launch<T, S>::upload_entries(int slot0, const void* entries, int n) {
+    return cudaMemcpyToSymbol(c_batch<T, S>, entries, n * sizeof(BatchEntry<T, S>),
+                              slot0 * sizeof(BatchEntry<T, S>), cudaMemcpyHostToDevice);
+}
+
+template <typename T, typename S>
+void Launch<T, S>::ghost_batched(int GK, const void* tabs, const int64_t* begin, int ndom, int64_t total, cudaStream_t s) {
+    if (total == 0) return;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (GK == 4) k_ghost_batched<4, T><<<blocks, 256, 0, s>>>((const GhostTable<T>*)tabs, begin, ndom, total);
+    else k_ghost_batched<8, T><<<blocks, 256, 0, s>>>((const GhostTable<T>*)tabs, begin, ndom, total);
+}
+
+template <typename T, typename S>
+void Launch<T, S>::fill_ghost_table(void* out, int64_t n, const int32_t* node, const int32_t* corner, const void* wt,
+                             double exp_eps, double eps, void* phi, int rule) {
+    GhostTable<T> g;
+    g.n = n; g.node = node; g.corner = corner; g.wt = (const T*)wt; g.exp_eps = (T)exp_eps; g.eps = (T)eps;
+    g.phi = (T*)phi; g.rule = rule;
+    std::memcpy(out, &g, sizeof(g));
+}
+
+template <typename T, typename S>
+int Launch<T, S>::diag_blocks(const Dims& d) {
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    int64_t b = (nn + DIAG_THREADS - 1) / DIAG_THREADS;
+    return (int)(b > DIAG_MAX_BLOCKS ? DIAG_MAX_BLOCKS : (b < 1 ? 1 : b));
+}
+
+template <typename T, typename S>
+void Launch<T, S>::diag(const StepConfig& c, const uint8_t* cls, const void* Nst, const void* phi, const void* u,
+                 const void* p, const ProbeDev& pr, double* partial, double* out, cudaStream_t s) {
+    const int nb = diag_blocks(c.d);
+    const StepParams<T> P = params(c);
+    if (c.Q == 9)
+        k_diag_partial<9, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, P, (const S*)Nst,
+                                                            (const T*)phi, (const T*)u, (const T*)p, pr, partial);
+    else
+        k_diag_partial<19, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, P, (const S*)Nst,
+                                                             (const T*)phi, (const T*)u, (const T*)p, pr, partial);
+    k_diag_final<<<1, 32, 0, s>>>(nb, partial, out);
+}
+
+}  // namespace lbmgpu

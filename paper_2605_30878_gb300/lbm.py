@@ -25,7 +25,9 @@ FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 EXPORTS = ("lbm_domain_bytes", "lbm_create_domain", "lbm_init_droplet", "lbm_init_phi", "lbm_step", "lbm_sync",
            "lbm_diagnostics", "lbm_read_state", "lbm_write_state", "lbm_profile_steps", "lbm_ghost_table", "lbm_ghost_fallbacks",
            "lbm_launches_per_step", "lbm_bytes_per_fluid_node", "lbm_fluid_nodes", "lbm_last_error", "lbm_destroy",
-           "lbm_phase_sums_noalloc")
+           "lbm_phase_sums_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_tune",
+           "lbm_batch_variant", "lbm_batch_set_variant", "lbm_batch_launches_per_step", "lbm_batch_last_error",
+           "lbm_batch_destroy")
 
 
 class LbmError(RuntimeError):
@@ -112,6 +114,24 @@ def load():
                                          C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_char_p,
                                          C.c_size_t]
     L.lbm_phase_sums_noalloc.restype = C.c_int
+    L.lbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]
+    L.lbm_batch_create.restype = C.c_int
+    L.lbm_batch_step.argtypes = [C.c_void_p, C.c_int64]
+    L.lbm_batch_step.restype = C.c_int
+    L.lbm_batch_sync.argtypes = [C.c_void_p]
+    L.lbm_batch_sync.restype = C.c_int
+    L.lbm_batch_tune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), _dp]
+    L.lbm_batch_tune.restype = C.c_int
+    L.lbm_batch_variant.argtypes = [C.c_void_p]
+    L.lbm_batch_variant.restype = C.c_int32
+    L.lbm_batch_set_variant.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_batch_set_variant.restype = C.c_int
+    L.lbm_batch_launches_per_step.argtypes = [C.c_void_p]
+    L.lbm_batch_launches_per_step.restype = C.c_int32
+    L.lbm_batch_last_error.argtypes = [C.c_void_p]
+    L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_batch_destroy.argtypes = [C.c_void_p]
+    L.lbm_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -324,3 +344,68 @@ class Domain:
 
     def fluid_nodes(self):
         return load().lbm_fluid_nodes(self.h)
+
+
+class Batch:
+    """Several domains (same lattice and precision) advanced by one launch per
+    phase; see lbm_batch_* in include/lbm.h.  Keeps references to
+    its domains so they outlive it."""
+
+    def __init__(self, domains, stream=None):
+        L = load()
+        self.domains = list(domains)
+        arr = (C.c_void_p * len(self.domains))(*[d.h.value for d in self.domains])
+        if stream is None:
+            stream = self.domains[0].stream_ptr
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        h = C.c_void_p()
+        st = L.lbm_batch_create(arr, len(self.domains), stream, C.byref(h))
+        if st != LBM_OK:
+            raise LbmError(st, L.lbm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, load().lbm_batch_last_error(self.h).decode())
+
+    def step(self, n=1):
+        self._check(load().lbm_batch_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(load().lbm_batch_sync(self.h))
+
+    def tune(self, steps_per_trial=20):
+        """Time every tile shape, keep the fastest; returns (chosen, ms per step of each)."""
+        ch = C.c_int32()
+        ms = np.zeros(3)
+        self._check(load().lbm_batch_tune(self.h, int(steps_per_trial), C.byref(ch), ms.ctypes.data_as(_dp)))
+        return ch.value, ms
+
+    @property
+    def variant(self):
+        return load().lbm_batch_variant(self.h)
+
+    def set_variant(self, v):
+        self._check(load().lbm_batch_set_variant(self.h, int(v)))
+
+    def launches_per_step(self):
+        return load().lbm_batch_launches_per_step(self.h)
+
+    def close(self):
+        """Wait for the batch's launches and give its constant-table slots back."""
+        if getattr(self, "h", None):
+            load().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

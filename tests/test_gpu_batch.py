@@ -1,0 +1,163 @@
+"""Batched launches (many uneven domains, one launch per phase, one block per
+tile) against the same domains stepped one by one: identical to the bit, for
+every tile shape the autotuner can pick, for both lattices and every storage
+precision."""
+import gc
+
+import numpy as np
+import pytest
+
+from paper_2605_30878_gb300 import lbm
+from paper_2605_30878_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_30878_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def _cases(precision, seed=4, count=5):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.integers(20, 44))
+        R = float(rng.uniform(0.2, 0.3) * n)
+        theta = float(rng.uniform(20, 160))
+        ratio = [1.0, 10.0, 1000.0][k % 3]
+        cfg = wl.sphere_config(n=n, R=R, R0=0.6 * R, theta_deg=theta, rho_ratio=ratio,
+                               mu_ratio=(100.0 if ratio > 1 else 1.0), precision=precision)
+        cfg["params"]["ghost_rule"] = k % 2
+        out.append(cfg)
+    return out
+
+
+def _make(cfgs):
+    doms = []
+    for c in cfgs:
+        d = lbm.Domain(c["params"], c["solid"], c["ghosts"])
+        d.init_droplet(c["drop_center"], c["R0"])
+        doms.append(d)
+    return doms
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
+def test_batch_equals_individual_steps(precision):
+    cfgs = _cases(precision)
+    alone = _make(cfgs)
+    for d in alone:
+        d.step(12)                        # 5 + 4 + 3 batched steps
+    mixed = _make(cfgs)
+    mixed[1].step(1)                      # domains may enter the batch at different parities
+    b = lbm.Batch(mixed)
+    b.set_variant(1)
+    b.step(5)
+    b.set_variant(2)
+    b.step(4)
+    b.set_variant(0)
+    b.step(3)
+    b.sync()
+    alone[1].step(1)                      # the extra step domain 1 took before joining
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        for f in ("N", "B", "phi", "u", "p"):
+            assert np.array_equal(a.read(f), m.read(f)), (k, f)
+
+def test_batch_rejects_outside_steps_and_mixed_precision():
+    cfgs = _cases(lbm.FP32, count=2)
+    doms = _make(cfgs)
+    with lbm.Batch(doms) as b:
+        doms[0].step(1)
+        with pytest.raises(lbm.LbmError) as e:
+            b.step(1)
+        assert e.value.status == lbm.LBM_ERR_ARG
+    other = _make(_cases(lbm.FP64, count=1))
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch([doms[1], other[0]])
+
+
+def test_autotuner_picks_a_shape_and_keeps_results():
+    cfgs = _cases(lbm.FP32, seed=9, count=4)
+    a, m = _make(cfgs), _make(cfgs)
+    b = lbm.Batch(m)
+    chosen, ms = b.tune(steps_per_trial=3)
+    assert chosen in (0, 1, 2) and (ms > 0).all() and b.variant == chosen
+    for d in a:
+        d.step(12)                        # tuning advanced every domain 3 x (3 + 1) steps
+    b.sync()
+    for x, y in zip(a, m):
+        assert np.array_equal(x.read("B"), y.read("B"))
+
+
+def _cases_2d(precision, seed=7, count=4):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        nx, ny = int(rng.integers(40, 150)), int(rng.integers(30, 90))
+        R = float(rng.uniform(0.1, 0.2) * min(nx, ny))
+        cfg = wl.cylinder_config(nx=nx, ny=ny, R=R, R0=0.8 * R, theta_deg=float(rng.uniform(20, 160)))
+        P = cfg["params"]
+        P["precision"] = precision
+        P["ghost_rule"] = k % 2
+        if k % 2:                               # density and viscosity contrast on every other case
+            P.update(rho_l=100.0, rho_g=1.0, mu_l=1.0, mu_g=0.1)
+        out.append(cfg)
+    return out
+
+
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
+def test_batch_equals_individual_steps_d2q9(precision):
+    cfgs = _cases_2d(precision)
+    alone, mixed = _make(cfgs), _make(cfgs)
+    for d in alone:
+        d.step(11)
+    b = lbm.Batch(mixed)
+    assert b.launches_per_step() == 4            # ghosts, contrast step, plain step, color
+    for v, n in ((2, 3), (1, 3), (0, 5)):
+        b.set_variant(v)
+        b.step(n)
+    b.sync()
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        for f in ("N", "B", "phi", "u", "p"):
+            assert np.array_equal(a.read(f), m.read(f)), (k, f)
+
+
+def test_two_live_batches_and_slot_reuse():
+    """Batches alive at the same time hold separate slots of the constant
+    parameter table; a closed batch's slots go to the next one."""
+    cfgs = _cases(lbm.FP32, seed=11, count=4)
+    alone, mixed = _make(cfgs), _make(cfgs)
+    b1, b2 = lbm.Batch(mixed[:2]), lbm.Batch(mixed[2:])
+    b1.step(3)
+    b2.step(5)
+    b1.close()
+    b3 = lbm.Batch(mixed[:1])                    # reuses a slot b1 held
+    b3.step(2)
+    b3.sync()
+    b2.sync()
+    for d, n in zip(alone, (5, 3, 5, 5)):
+        d.step(n)
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(a.read("N"), m.read("N")), k
+        assert np.array_equal(a.read("phi"), m.read("phi")), k
+
+
+def test_batch_size_limit():
+    """At most 96 domains per batch (the constant table's slots per precision)."""
+    cfg = wl.sphere_config(n=12, R=3.0, R0=2.5, theta_deg=90.0, rho_ratio=1.0, mu_ratio=1.0, precision=lbm.FP32)
+    gc.collect()                                 # batches of earlier tests give their slots back
+    doms = _make([cfg] * 97)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Batch(doms)
+    assert e.value.status == lbm.LBM_ERR_ARG and "96" in str(e.value)
+    with lbm.Batch(doms[:96]) as b:
+        b.step(2)
+        b.sync()
+    a = _make([cfg])[0]
+    a.step(2)
+    assert np.array_equal(a.read("N"), doms[95].read("N"))
