@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-case batched measurement")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the served workload (Poisson arrivals at 20/s); 0 skips it")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="population storage: fp32 (the bench default) or fp16 (shifted, scaled)")
     return ap.parse_args()
@@ -282,6 +284,29 @@ def run_batch_bench(lbm, steps):
     return res
 
 
+def run_serve_bench(n_requests):
+    """The served workload: Poisson arrivals at 20/s (seed 3), half D2Q9 drops
+    on cylinders (L ~ U{128..1024}^2), half D3Q19 drops on spheres
+    (L ~ U{64..192}^3), theta ~ U(20, 160) deg, density ratio log-uniform on
+    [1, 1000], FP32; each case runs until its contact angle moves less than
+    0.1 deg per 1000 steps (cap 20000 steps).  Memory budget: 60% of the free
+    device memory."""
+    import torch
+    from paper_2605_30878_gb300 import serve
+    reqs = serve.poisson_requests(n=n_requests)
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(serve.GpuBackend(), memory_budget=int(0.6 * free))
+    res, summ = srv.run(reqs)
+    errs = [abs(r.theta_measured - r.theta_set) for r in res if r.converged]
+    out = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
+    out.update({"unit_latency": "s from arrival to converged", "mlups_unit": "fluid-node MLUPS over the served span",
+                "theta_err_vs_set_deg": {"median": float(np.median(errs)) if errs else None,
+                                         "max": float(np.max(errs)) if errs else None},
+                "memory_budget_gb": round(srv.memory_budget / 1e9, 1)})
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -395,7 +420,16 @@ def run_ours(args):
 
         batched = None
         if world == 1 and not args.no_batch:
-            batched = run_batch_bench(lbm, args.batch_steps)
+            try:
+                batched = run_batch_bench(lbm, args.batch_steps)
+            except Exception as exc:                       # reported in the line, not fatal to it
+                batched = {"error": repr(exc)}
+        serving = None
+        if world == 1 and args.serve_requests > 0:
+            try:
+                serving = run_serve_bench(args.serve_requests)
+            except Exception as exc:
+                serving = {"error": repr(exc)}
 
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -424,6 +458,7 @@ def run_ours(args):
             "clocks": clk,
             "contact_angle": angle,
             "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -802,7 +802,7 @@ struct lbm_batch {
     int ntiles[kTileVariants] = {0, 0, 0};
     int ncontrast[kTileVariants] = {0, 0, 0};   // tiles of domains with density contrast come first
     int device = 0;
-    int slot0 = -1;                    // first of doms.size() slots of the constant table
+    std::vector<int> slots;            // each domain's slot of the constant table
     char* dev = nullptr;               // one allocation for every device table
     int4* tiles[kTileVariants] = {nullptr, nullptr, nullptr};   // {slot, x0, y0, z0}
     void* ghost_tabs = nullptr;
@@ -822,31 +822,29 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& m) {
     return s;
 }
 
-// Slots of the constant tables (one table per precision and GPU), handed out
-// as contiguous ranges, first fit.
+// Slots of the constant tables (one table per precision and GPU).  A batch
+// takes any n free slots (the tile list names each tile's slot, so they need
+// not be contiguous); an empty vector means fewer than n are free.
 std::mutex g_slot_mutex;
 std::map<std::pair<int, int>, std::vector<char>> g_slots_used;
 
-int reserve_slots(int device, int precision, int n) {
+std::vector<int> reserve_slots(int device, int precision, int n) {
     std::lock_guard<std::mutex> lk(g_slot_mutex);
     std::vector<char>& used = g_slots_used[{device, precision}];
     used.resize(kBatchSlots, 0);
-    for (int s0 = 0; s0 + n <= kBatchSlots; ++s0) {
-        int k = 0;
-        while (k < n && !used[s0 + k]) ++k;
-        if (k == n) {
-            for (k = 0; k < n; ++k) used[s0 + k] = 1;
-            return s0;
-        }
-        s0 += k;
-    }
-    return -1;
+    std::vector<int> got;
+    for (int k = 0; k < kBatchSlots && (int)got.size() < n; ++k)
+        if (!used[k]) got.push_back(k);
+    if ((int)got.size() < n) return {};
+    for (int k : got) used[k] = 1;
+    return got;
 }
 
-void release_slots(int device, int precision, int s0, int n) {
+void release_slots(int device, int precision, const std::vector<int>& slots) {
     std::lock_guard<std::mutex> lk(g_slot_mutex);
     std::vector<char>& used = g_slots_used[{device, precision}];
-    for (int k = 0; k < n && s0 + k < (int)used.size(); ++k) used[s0 + k] = 0;
+    for (int k : slots)
+        if (k >= 0 && k < (int)used.size()) used[k] = 0;
 }
 
 template <typename F>
@@ -926,8 +924,8 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
         return bfail(nullptr, LBM_ERR_ARG, "a batch holds at most " + std::to_string(kBatchSlots) + " domains");
     }
     cudaGetDevice(&b->device);
-    b->slot0 = reserve_slots(b->device, b->precision, n);
-    if (b->slot0 < 0) {
+    b->slots = reserve_slots(b->device, b->precision, n);
+    if (b->slots.empty()) {
         delete b;
         return bfail(nullptr, LBM_ERR_OOM, "no " + std::to_string(n) + " free slots left in the constant table (" +
                                                std::to_string(kBatchSlots) + " per precision, shared by live batches)");
@@ -964,7 +962,7 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
         for (int i = 0; i < n; ++i) {
             if (b->doms[i]->contrast != (pass == 0)) continue;
             for (int V = 0; V < kTileVariants; ++V) {
-                append_tiles(b->Q, V, b->doms[i]->prm, b->slot0 + i, tiles[V]);
+                append_tiles(b->Q, V, b->doms[i]->prm, b->slots[i], tiles[V]);
                 if (pass == 0) b->ncontrast[V] = (int)tiles[V].size();
             }
         }
@@ -988,7 +986,8 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
     b->ghost_tabs = b->dev + o_g;
     b->ghost_begin = (int64_t*)(b->dev + o_gb);
     cudaError_t e = cudaSuccess;
-    bdispatch(b->precision, [&](auto Lx) { e = decltype(Lx)::upload_entries(b->slot0, he.data(), n); });
+    for (int i = 0; i < n && e == cudaSuccess; ++i)
+        bdispatch(b->precision, [&](auto Lx) { e = decltype(Lx)::upload_entries(b->slots[i], &he[esz * i], 1); });
     if (e == cudaSuccess) e = cudaMemcpy(b->ghost_tabs, hg.data(), hg.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->ghost_begin, gbegin.data(), gbegin.size() * 8, cudaMemcpyHostToDevice);
     for (int V = 0; V < kTileVariants && e == cudaSuccess; ++V) {
@@ -1096,9 +1095,9 @@ const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str()
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     // the slots may be handed to another batch: let this batch's launches finish first
-    if (b->slot0 >= 0) {
+    if (!b->slots.empty()) {
         cudaStreamSynchronize(b->stream);
-        release_slots(b->device, b->precision, b->slot0, (int)b->doms.size());
+        release_slots(b->device, b->precision, b->slots);
     }
     for (auto* g : {b->g1[0], b->g1[1], b->g8})
         if (g) cudaGraphExecDestroy(g);

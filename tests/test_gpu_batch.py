@@ -161,3 +161,15 @@ def test_batch_size_limit():
     a = _make([cfg])[0]
     a.step(2)
     assert np.array_equal(a.read("N"), doms[95].read("N"))
+    # slots need not be contiguous: free slot 0 and slot 95 around a live batch
+    b1, b2 = lbm.Batch(doms[0:1]), lbm.Batch(doms[1:95])
+    b1.close()
+    with lbm.Batch(doms[95:97]) as b3:
+        b3.step(3)
+        b3.sync()
+    b2.close()
+    a.step(3)
+    assert np.array_equal(a.read("N"), doms[95].read("N"))
+    a2 = _make([cfg])[0]
+    a2.step(3)
+    assert np.array_equal(a2.read("N"), doms[96].read("N"))
