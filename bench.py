@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the served workload (Poisson arrivals at 20/s); 0 skips it")
+    ap.add_argument("--serve-plain", action="store_true",
+                    help="also serve the same stream with per-case launches instead of batches")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="population storage: fp32 (the bench default) or fp16 (shifted, scaled)")
     return ap.parse_args()
@@ -284,7 +286,7 @@ def run_batch_bench(lbm, steps):
     return res
 
 
-def run_serve_bench(n_requests):
+def run_serve_bench(n_requests, batched=True):
     """The served workload: Poisson arrivals at 20/s (seed 3), half D2Q9 drops
     on cylinders (L ~ U{128..1024}^2), half D3Q19 drops on spheres
     (L ~ U{64..192}^3), theta ~ U(20, 160) deg, density ratio log-uniform on
@@ -295,7 +297,7 @@ def run_serve_bench(n_requests):
     from paper_2605_30878_gb300 import serve
     reqs = serve.poisson_requests(n=n_requests)
     free, _ = torch.cuda.mem_get_info()
-    srv = serve.Server(serve.GpuBackend(), memory_budget=int(0.6 * free))
+    srv = serve.Server(serve.GpuBackend(batched=batched), memory_budget=int(0.6 * free))
     res, summ = srv.run(reqs)
     errs = [abs(r.theta_measured - r.theta_set) for r in res if r.converged]
     out = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in summ.items()}
@@ -428,6 +430,8 @@ def run_ours(args):
         if world == 1 and args.serve_requests > 0:
             try:
                 serving = run_serve_bench(args.serve_requests)
+                if args.serve_plain:
+                    serving["per_case_launches"] = run_serve_bench(args.serve_requests, batched=False)
             except Exception as exc:
                 serving = {"error": repr(exc)}
 

@@ -490,31 +490,15 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
         return fail(nullptr, LBM_ERR_CUDA, msg);
     };
     if (cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking) != cudaSuccess) return bail("cudaStreamCreate failed");
-    // upload node classes and the ghost table
-    // per-node bounce-back mask: bit i set when x - c_i is not fluid; top bit for non-fluid x
-    std::vector<uint32_t> hmask(nn, MASK_NOT_FLUID);
-    for (int64_t z = 0; z < nz; ++z)
-        for (int64_t y = 0; y < ny; ++y)
-            for (int64_t x = 0; x < nx; ++x) {
-                const int64_t node = x + nx * (y + ny * z);
-                if (d->h_cls[node] != CLS_FLUID) continue;
-                uint32_t m = 0;
-                for (int i = 1; i < P.lattice; ++i) {
-                    const int cx = P.lattice == 9 ? Lattice<9>::cx(i) : Lattice<19>::cx(i);
-                    const int cy = P.lattice == 9 ? Lattice<9>::cy(i) : Lattice<19>::cy(i);
-                    const int cz = P.lattice == 9 ? Lattice<9>::cz(i) : Lattice<19>::cz(i);
-                    const int64_t xx = (x - cx + nx) % nx, yy = (y - cy + ny) % ny, zz = (z - cz + nz) % nz;
-                    if (d->h_cls[xx + nx * (yy + ny * zz)] != CLS_FLUID) m |= 1u << i;
-                }
-                hmask[node] = m;
-            }
+    // upload node classes and the ghost table; the bounce-back mask is built on the device
     std::vector<int32_t> gnode(n_ghosts);
     for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)ghosts[g].node;
     cudaStream_t s = d->stream;
     if (cudaMemsetAsync(d->ws, 0, L.total, s) != cudaSuccess) return bail("cudaMemset failed");
-    if (cudaMemcpyAsync(d->cls(), d->h_cls.data(), nn, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d->mask(), hmask.data(), nn * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(d->cls(), d->h_cls.data(), nn, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return bail("upload of node classes failed");
+    dispatch(d, [&](auto Lx) { decltype(Lx)::build_mask(d->cfg, d->cls(), d->mask(), s); });
+    if (cudaGetLastError() != cudaSuccess) return bail("launch of the mask kernel failed");
     if (n_ghosts > 0) {
         if (cudaMemcpyAsync(d->at<void>(L.off_gnode), gnode.data(), n_ghosts * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(d->at<void>(L.off_gcorner), d->h_corner.data(), d->h_corner.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)

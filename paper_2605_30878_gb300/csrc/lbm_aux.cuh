@@ -25,6 +25,33 @@ __device__ __forceinline__ int64_t shifted(const Dims& d, int x, int y, int z, i
     return xx + (int64_t)d.nx * (yy + (int64_t)d.ny * zz);
 }
 
+// Per-node bounce-back mask from the node classes: bit i (1 <= i < Q) set when
+// x - c_i (periodic wrap) is not a fluid node, MASK_NOT_FLUID for non-fluid x.
+template <int Q>
+__global__ void k_build_mask(Dims d, const uint8_t* __restrict__ cls, uint32_t* __restrict__ mask) {
+    using L = Lattice<Q>;
+    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
+         node += (int64_t)gridDim.x * blockDim.x) {
+        if (cls[node] != CLS_FLUID) {
+            mask[node] = MASK_NOT_FLUID;
+            continue;
+        }
+        int x, y, z;
+        node_xyz(node, d, x, y, z);
+        uint32_t m = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            int xx = x - L::cx(i), yy = y - L::cy(i), zz = z - L::cz(i);
+            xx += xx < 0 ? d.nx : (xx >= d.nx ? -d.nx : 0);
+            yy += yy < 0 ? d.ny : (yy >= d.ny ? -d.ny : 0);
+            zz += zz < 0 ? d.nz : (zz >= d.nz ? -d.nz : 0);
+            if (cls[xx + (int64_t)d.nx * (yy + (int64_t)d.ny * zz)] != CLS_FLUID) m |= 1u << i;
+        }
+        mask[node] = m;
+    }
+}
+
 // Color at t = 0 (Eq. equilibriumPhaseField and the ghost value of Sec. III).
 // mode 0: drop of radius R0 at centre; mode 1: keep the fluid values already in phi.
 template <int D, typename T>

@@ -59,6 +59,7 @@ struct Launch {
     static void init_phi(const StepConfig& c, const uint8_t* cls, void* phi, int mode, const double ctr[3], double R0,
                          double ghost_value, cudaStream_t s);
     static void init_pops(const StepConfig& c, const uint8_t* cls, const void* phi, void* N, void* B, cudaStream_t s);
+    static void build_mask(const StepConfig& c, const uint8_t* cls, uint32_t* mask, cudaStream_t s);
     // base subtracted from direction i of N (is_b = false) or B (true) in storage
     static double storage_base(const StepConfig& c, int i, bool is_b);
     static void scatter_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* post_i,

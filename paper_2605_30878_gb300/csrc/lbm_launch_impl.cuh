@@ -106,6 +106,14 @@ void Launch<T, S>::init_pops(const StepConfig& c, const uint8_t* cls, const void
         k_init_pops<19, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, P, cls, (const T*)phi, (S*)N, (S*)B);
 }
 
+template <typename T, typename S>
+void Launch<T, S>::build_mask(const StepConfig& c, const uint8_t* cls, uint32_t* mask, cudaStream_t s) {
+    if (c.Q == 9)
+        k_build_mask<9><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, mask);
+    else
+        k_build_mask<19><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, mask);
+}
+
 // base subtracted from direction i of N (is_b = false) or B (true) in storage
 template <typename T, typename S>
 double Launch<T, S>::storage_base(const StepConfig& c, int i, bool is_b) {

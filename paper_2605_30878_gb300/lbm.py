@@ -187,13 +187,16 @@ def phase_sums_noalloc(dev_class, dev_phi, dev_u, precision, n_components, n_nod
         raise LbmError(st, err.value.decode())
 
 
+_GHOST_DTYPE = np.dtype([("node", "<i8"), ("n", "<f8", (3,))])       # the layout of lbm_ghost
+
+
 def ghost_array(nodes, normals):
-    nodes = np.asarray(nodes, dtype=np.int64)
+    """A contiguous lbm_ghost array (as a numpy record array) and its length."""
+    nodes = np.asarray(nodes, dtype=np.int64).reshape(-1)
     normals = np.asarray(normals, dtype=np.float64).reshape(-1, 3)
-    arr = (Ghost * max(1, len(nodes)))()
-    for k in range(len(nodes)):
-        arr[k].node = int(nodes[k])
-        arr[k].n[:] = [float(v) for v in normals[k]]
+    arr = np.zeros(max(1, len(nodes)), dtype=_GHOST_DTYPE)
+    arr["node"][:len(nodes)] = nodes
+    arr["n"][:len(nodes)] = normals
     return arr, len(nodes)
 
 
@@ -247,7 +250,7 @@ class Domain:
             stream_ptr = int(stream)
         self.stream_ptr = stream_ptr
         h = C.c_void_p()
-        st = L.lbm_create_domain(C.byref(P), solid.ctypes.data, C.cast(garr, C.c_void_p), ng,
+        st = L.lbm_create_domain(C.byref(P), solid.ctypes.data, garr.ctypes.data, ng,
                                  ws_ptr, ws_bytes, stream_ptr, C.byref(h))
         _check(st, None)
         self.h = h

@@ -99,14 +99,16 @@ def request_case(req, precision=1, sigma=0.01, W=4.0, M_phi=0.02, solid_frac=0.1
 
 class GpuBackend:
     """Cases are lbm.Domain objects; each lattice's cases share one CUDA stream
-    and one lbm.Batch."""
+    and one lbm.Batch (batched=True), or are stepped one after the other by
+    their own launches (batched=False, the per-case baseline)."""
 
-    def __init__(self, precision=1, exclude=6.0, keep_final=False):
+    def __init__(self, precision=1, exclude=6.0, keep_final=False, batched=True):
         """exclude: interface points nearer the solid than min(exclude, half
         the drop's initial cap height) are left out of the contact-angle fit."""
         import torch
         from . import lbm
         self.lbm, self.torch = lbm, torch
+        self.batched = batched
         self.precision = precision
         self.exclude = exclude
         self.keep_final = keep_final                     # keep each case's final color field (tests)
@@ -127,18 +129,29 @@ class GpuBackend:
         return dict(domain=d, probe=probe, rid=req.rid)
 
     def batch(self, lattice, handles):
+        if not self.batched:
+            return [h["domain"] for h in handles]
         return self.lbm.Batch([h["domain"] for h in handles], stream=self.streams[lattice])
 
     def close_batch(self, b):
-        b.close()
+        if self.batched:
+            b.close()
 
     def launch(self, batches, n):
-        for b in batches:
-            b.step(n)                                    # asynchronous; the lattices overlap
+        for b in batches:                                # asynchronous; the lattices overlap
+            if self.batched:
+                b.step(n)
+            else:
+                for d in b:
+                    d.step(n)
 
     def wait(self, batches):
         for b in batches:
-            b.sync()
+            if self.batched:
+                b.sync()
+            else:
+                for d in b:
+                    d.sync()
 
     def angle_deg(self, h):
         """Contact angle in degrees; NaN when no interface could be fitted, None
@@ -202,11 +215,19 @@ class Server:
         node_steps = 0
         n_rebuilds = 0
         peak_active = 0
+        phase = collections.Counter()                            # host seconds per phase of the loop
+
+        def timed(name, fn, *a):
+            t1 = self.clock()
+            out = fn(*a)
+            phase[name] += self.clock() - t1
+            return out
+
         def arrivals():
             t = now()
             while pending and pending[0].arrival <= t:
                 q = pending.popleft()
-                waiting.append((q, be.prepare(q)))
+                waiting.append((q, timed("prepare", be.prepare, q)))
 
         while pending or waiting or active[9] or active[19]:
             arrivals()
@@ -219,7 +240,7 @@ class Server:
                 if used_bytes + case["bytes"] > self.memory_budget or n_act >= self.max_active:
                     break
                 waiting.popleft()
-                h = be.open(q, case)
+                h = timed("open", be.open, q, case)
                 used_bytes += case["bytes"]
                 active[q.lattice].append(dict(req=q, h=h, bytes=case["bytes"], steps=0, prev=None,
                                               fluid=case["fluid_nodes"]))
@@ -229,20 +250,20 @@ class Server:
             peak_active = max(peak_active, len(active[9]) + len(active[19]))
             if not (active[9] or active[19]):
                 if pending:
-                    self.sleep(max(0.0, min(pending[0].arrival - now(), 0.05)))
+                    timed("idle", self.sleep, max(0.0, min(pending[0].arrival - now(), 0.05)))
                 continue
             for lat in dirty:                                     # close first: their slots are reused
                 if lat in batches:
-                    be.close_batch(batches.pop(lat))
+                    timed("rebuild", be.close_batch, batches.pop(lat))
             for lat in dirty:
                 if active[lat]:
-                    batches[lat] = be.batch(lat, [e["h"] for e in active[lat]])
+                    batches[lat] = timed("rebuild", be.batch, lat, [e["h"] for e in active[lat]])
                     n_rebuilds += 1
             dirty.clear()
             running = [batches[lat] for lat in (9, 19) if lat in batches]
-            be.launch(running, self.chunk)
+            timed("launch", be.launch, running, self.chunk)
             arrivals()                                    # host-side set-up overlaps the chunk
-            be.wait(running)
+            timed("wait", be.wait, running)
             for lat in (9, 19):
                 keep = []
                 for e in active[lat]:
@@ -250,7 +271,7 @@ class Server:
                     node_steps += e["fluid"] * self.chunk
                     done = False
                     if e["steps"] % self.check_every == 0:
-                        th = be.angle_deg(e["h"])
+                        th = timed("check", be.angle_deg, e["h"])
                         r = results[e["req"].rid]
                         if th is None:                           # non-finite state: the case failed
                             done, r.failed = True, True
@@ -264,7 +285,7 @@ class Server:
                     if done:
                         r = results[e["req"].rid]
                         r.finished, r.steps = now(), e["steps"]
-                        be.close(e["h"])
+                        timed("retire", be.close, e["h"])
                         used_bytes -= e["bytes"]
                         dirty.add(lat)
                     else:
@@ -284,5 +305,6 @@ class Server:
                        p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
                        mean_s=float(lat.mean()), mlups=node_steps / wall / 1e6 if wall > 0 else 0.0,
                        node_steps=int(node_steps), batch_rebuilds=n_rebuilds, peak_active=peak_active,
-                       steps_mean=float(np.mean([r.steps for r in res])))
+                       steps_mean=float(np.mean([r.steps for r in res])) if res else 0.0,
+                       host_seconds={k: round(v, 3) for k, v in sorted(phase.items())})
         return res, summary

@@ -96,3 +96,16 @@ def test_validation_before_any_device_call(L):
     e = _create_error(dict(P, M_phi=1.0), solid, (nodes, normals))          # alpha < 0
     assert e.status == lbm.LBM_ERR_ARG and "alpha" in str(e)
     assert "alpha" in lbm.last_error(None)
+
+
+def test_ghost_records_have_the_lbm_ghost_layout():
+    """The binding hands lbm_create_domain a numpy record array; its layout is
+    that of lbm_ghost (int64 node, then three doubles)."""
+    import ctypes as C
+    from paper_2605_30878_gb300 import lbm
+    arr, n = lbm.ghost_array([5, 7], [[1, 0, 0], [0, 0.6, 0.8]])
+    assert n == 2 and arr.dtype.itemsize == C.sizeof(lbm.Ghost) == 32
+    g = (lbm.Ghost * 2).from_buffer(arr)
+    assert g[1].node == 7 and list(g[1].n) == [0.0, 0.6, 0.8]
+    empty, n0 = lbm.ghost_array(np.zeros(0, np.int64), np.zeros((0, 3)))
+    assert n0 == 0 and len(empty) == 1
