@@ -54,12 +54,25 @@ def parse():
                     help="requests of the served workload (Poisson arrivals at 20/s); 0 skips it")
     ap.add_argument("--serve-plain", action="store_true",
                     help="also serve the same stream with per-case launches instead of batches")
+    ap.add_argument("--no-table", action="store_true", help="skip the paper's Table I grids")
+    ap.add_argument("--table-steps", type=int, default=2000)
+    ap.add_argument("--packing-steps", type=int, default=0,
+                    help="run the 256^3 sphere-packing imbibition for this many steps in FP64, FP32 and "
+                         "FP16 storage (0 skips it)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16"],
                     help="population storage: fp32 (the bench default) or fp16 (shifted, scaled)")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ helpers
+
+_T0 = time.perf_counter()
+
+
+def note(phase):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print("[bench %7.1f s] %s" % (time.perf_counter() - _T0, phase), file=sys.stderr, flush=True)
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
@@ -286,6 +299,112 @@ def run_batch_bench(lbm, steps):
     return res
 
 
+def time_domain(dom, steps, warmup=20):
+    """Seconds per step of dom.step over `steps` steps (CUDA events on its stream)."""
+    import torch
+    dom.step(warmup)
+    dom.sync()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    dom.step(steps)
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / steps
+
+
+def run_paper_table(lbm, steps):
+    """The paper's Table I grids of its two static wetting benchmarks (drop on
+    a flat plate: walls at y = 0 and y = ny-1, periodic x, drop area 1e4 at
+    500 x 300 scaled with the grid; drop on a cylinder: R = 0.2 L at the box
+    centre, drop on its top, all periodic), density ratio 1000, viscosity ratio
+    100, FP32 and FP64, MLUPS on every grid node as the paper counts them.  The
+    smaller grids fit in the 129 MB L2."""
+    from paper_2605_30878_gb300 import workloads as wl
+    out = {}
+    for name, nx, ny in (("plate", 500, 300), ("plate", 1000, 600), ("plate", 1500, 900),
+                         ("cylinder", 201, 201), ("cylinder", 401, 401), ("cylinder", 601, 601)):
+        shape = (1, ny, nx)
+        if name == "plate":
+            solid, ghosts = wl.wall_domain(9, shape, 1, 1)
+            periodic = 1
+            scale = nx / 500.0
+            r = math.sqrt(1e4 / math.pi) * scale
+            center = (nx / 2.0, 1.0 + 0.6 * r, 0.0)
+        else:
+            R = 0.2 * nx
+            solid, ghosts = wl.sphere_domain(9, shape, (nx / 2.0, ny / 2.0, 0.0), R)
+            periodic = 7
+            r = 0.5 * R
+            center = (nx / 2.0, ny / 2.0 + R + 0.5 * r, 0.0)
+        row = {}
+        for prec, key in ((lbm.FP32, "fp32"), (lbm.FP64, "fp64")):
+            P = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=periodic, precision=prec, rho_l=1000.0, rho_g=1.0,
+                     mu_l=10.0, mu_g=0.1, sigma=0.01, W=4.0, M_phi=0.02, theta=math.radians(60.0))
+            d = lbm.Domain(P, solid, ghosts)
+            d.init_droplet(center, r)
+            sec = time_domain(d, steps)
+            row[key + "_mlups"] = round(nx * ny / sec / 1e6, 1)
+            d.close()
+        out["%s %dx%d" % (name, nx, ny)] = row
+    return out
+
+
+def run_packing_bench(lbm, steps, checkpoints=10, fp64_steps=1000):
+    """The 256^3 sphere packing (radii U(8, 16), porosity 0.45 in x >= 24,
+    seed 1): liquid slab 0 <= x < 16 (tanh, periodic image included) in the
+    sphere-free reservoir, theta = 45 deg, density and viscosity ratio 1,
+    sigma = 0.01, all periodic.  FP32 and FP16 population storage run `steps`
+    steps; FP64 (about 45x slower on this GPU, whose FP64 units are few) runs
+    the first `fp64_steps` as the reference.  Reported: the liquid saturation
+    of the packing region (sum of phi over its fluid nodes / their count) at
+    each checkpoint, its deviation from FP64 and from FP32, the phase-mass
+    drift and MLUPS (every node of the grid)."""
+    import torch
+    from paper_2605_30878_gb300 import workloads as wl
+    n = 256
+    c, rad = wl.sphere_packing(n=n)
+    solid, ghosts = wl.packing_domain(c, rad, n=n)
+    fluid = solid.reshape(-1) == 0
+    x = np.tile(np.arange(n), n * n)
+    region = fluid & (x >= 24)
+    d_slab = np.minimum(np.abs(x - 7.5), n - np.abs(x - 7.5))        # periodic distance to the slab centre
+    phi0 = wl.tanh_field(8.0 - d_slab, 4.0)
+    ref_marks = [fp64_steps // 2, fp64_steps]
+    marks = sorted(set(ref_marks + [steps * (k + 1) // checkpoints for k in range(checkpoints)]))
+    out = {"porosity_packing_region": float(1.0 - solid[:, :, 24:].mean()), "spheres": int(len(rad)),
+           "ghost_nodes": int(len(ghosts[0])), "steps": steps, "checkpoints": marks}
+    sat = {}
+    for prec, key, last in ((lbm.FP32, "fp32", steps), (lbm.FP16, "fp16", steps), (lbm.FP64, "fp64", fp64_steps)):
+        P = dict(lattice=19, nx=n, ny=n, nz=n, periodic=7, precision=prec, rho_l=1.0, rho_g=1.0, mu_l=0.1,
+                 mu_g=0.1, sigma=0.01, W=4.0, M_phi=0.02, theta=math.radians(45.0))
+        d = lbm.Domain(P, solid, ghosts)
+        d.init_phi(phi0)
+        m0 = d.diagnostics()["phi_sum"]
+        sat[key] = []
+        gpu_s, done = 0.0, 0
+        for mk in marks:
+            if mk > last:
+                break
+            gpu_s += time_domain(d, mk - done, warmup=0) * (mk - done)
+            done = mk
+            sat[key].append(float(d.read("phi")[region].mean()))
+        dg = d.diagnostics()
+        out[key] = {"steps": done, "mlups": round(n ** 3 * done / gpu_s / 1e6, 1),
+                    "phi_sum_drift_rel": (dg["phi_sum"] - m0) / m0, "max_u": dg["max_u"], "nan_flag": dg["nan_flag"]}
+        print("packing", key, out[key], file=sys.stderr, flush=True)
+        d.close()
+        torch.cuda.empty_cache()
+    out["saturation"] = sat
+    k64 = len(sat["fp64"])
+    for key in ("fp32", "fp16"):
+        out[key]["saturation_max_abs_dev_vs_fp64"] = float(np.max(np.abs(np.array(sat[key][:k64]) -
+                                                                       np.array(sat["fp64"]))))
+    out["fp16"]["saturation_max_abs_dev_vs_fp32"] = float(np.max(np.abs(np.array(sat["fp16"]) -
+                                                                        np.array(sat["fp32"]))))
+    return out
+
+
 def run_serve_bench(n_requests, batched=True):
     """The served workload: Poisson arrivals at 20/s (seed 3), half D2Q9 drops
     on cylinders (L ~ U{128..1024}^2), half D3Q19 drops on spheres
@@ -414,18 +533,35 @@ def run_ours(args):
         h2d = nn + ng * (4 + 8 * 4 + 8 * s)
         d2h = 32 * 8 + 4
 
+        note("cpu")
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             rate, st, dt = time_oracle(cfg, 10.0, 6)
             cpu = {"value": rate, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
                    "sample": "%d FP64 oracle steps of the %d^3 workload after 1 warm-up step (%.1f s)" % (st, n, dt)}
 
+        note("batched")
         batched = None
         if world == 1 and not args.no_batch:
             try:
                 batched = run_batch_bench(lbm, args.batch_steps)
             except Exception as exc:                       # reported in the line, not fatal to it
                 batched = {"error": repr(exc)}
+        note("table")
+        table = None
+        if world == 1 and not args.no_table:
+            try:
+                table = run_paper_table(lbm, args.table_steps)
+            except Exception as exc:
+                table = {"error": repr(exc)}
+        note("packing")
+        packing = None
+        if world == 1 and args.packing_steps > 0:
+            try:
+                packing = run_packing_bench(lbm, args.packing_steps)
+            except Exception as exc:
+                packing = {"error": repr(exc)}
+        note("serving")
         serving = None
         if world == 1 and args.serve_requests > 0:
             try:
@@ -463,6 +599,8 @@ def run_ours(args):
             "contact_angle": angle,
             "batched": batched,
             "serving": serving,
+            "paper_table1": table,
+            "packing": packing,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
