@@ -183,6 +183,18 @@ struct Wrap {
 // Load a block's color (and optionally velocity) tile with a one-node halo.
 // Ghost nodes hold their fresh ghost color; the velocity at solid nodes is 0
 // in memory (never written), so no node class is needed here.
+// One 4- or 8-byte value global -> shared without a register round trip
+// (cp.async); it lands at the next cp_async_wait_all.
+template <typename T>
+__device__ __forceinline__ void cp_async_value(T* dst_shared, const T* src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async copies 4, 8 or 16 bytes");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_shared);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"((int)sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Issues the copies of the halo tile; the caller waits (cp_async_wait_all,
+// then a barrier) before reading it.
 template <int Q, int V, typename T, bool LOAD_U>
 __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __restrict__ phi,
                                           const T* __restrict__ u, T* s_phi, T* s_u, int x0, int y0, int z0) {
@@ -203,10 +215,10 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __res
         const int sbase = Tl::HX * r;
         for (int e = lane; e < Tl::HX; e += 32) {
             const int node = rowbase + wrap_halo(x0 + e - 1, P.nx);
-            s_phi[sbase + e] = phi[node];
+            cp_async_value(s_phi + sbase + e, phi + node);
             if (LOAD_U) {
 #pragma unroll
-                for (int d = 0; d < D; ++d) s_u[d * Tl::HN + sbase + e] = u[d * uplane + node];
+                for (int d = 0; d < D; ++d) cp_async_value(s_u + d * Tl::HN + sbase + e, u + d * uplane + node);
             }
         }
     }
@@ -393,37 +405,39 @@ __device__ __forceinline__ void node_update_literal(const StepParams<double>& P,
     }
 }
 
-// One fluid node of the step, reading the block's halo tile (already loaded).
+// Pull the post-streaming populations N of fluid node (x, y, z) with mask m
+// (bounce-back where x - c_i is solid).  B enters the collision only through
+// phi = sum B, which k_phi computed.  Full values for FP64 storage,
+// deviations N_i - chi_i otherwise.
+template <int Q, typename T, typename S>
+__device__ __forceinline__ void pull_node(const StepParams<T>& P, const S* __restrict__ Nin, uint32_t m, int node,
+                                          int x, int y, int z, T (&N)[Q]) {
+    using L = Lattice<Q>;
+    using PS = PopStore<S>;
+    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz);
+    const int pl = (int)P.plane;
+    N[0] = (T)PS::load_rest(PS::rest(Nin), node);
+    const auto* mv = PS::moving(Nin, pl);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int idx = ((m >> i) & 1u) ? (L::opp(i) - 1) * pl + node
+                                        : (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i));
+        N[i] = (T)PS::load_moving(mv, idx, kScaleN);
+    }
+}
+
+// One fluid node of the step: pulled populations N, the block's halo tile.
 template <int Q, int V, typename T, typename S, bool CONTRAST>
 __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuffers<T, S>& b,
-                                          const T* __restrict__ s_phi, const T* __restrict__ s_u, int x, int y, int z) {
+                                          const T* __restrict__ s_phi, const T* __restrict__ s_u, const T (&N)[Q],
+                                          int node) {
     using L = Lattice<Q>;
     using Tl = Tile<Q, V>;
     constexpr int D = L::D;
-    if (x >= P.nx || y >= P.ny || z >= P.nz) return;
-    const int node = x + P.nx * (y + P.ny * z);
-    const uint32_t m = __ldg(b.mask + node);
-    if (m & MASK_NOT_FLUID) return;
     const int hc = (threadIdx.x + 1) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (D == 2 ? 0 : threadIdx.z + 1));
-    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz);
     const int pl = (int)P.plane;
-
-    // pull the post-streaming populations N (bounce-back where x - c_i is solid);
-    // B enters the collision only through phi = sum B, which k_phi computed
-    // (full values for FP64 storage, deviations N_i - chi_i otherwise)
     using PS = PopStore<S>;
     constexpr bool kShift = PS::kShift;
-    T N[Q];
-    N[0] = (T)PS::load_rest(PS::rest(b.Nin), node);
-    {
-        const auto* mv = PS::moving(b.Nin, pl);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int idx = ((m >> i) & 1u) ? (L::opp(i) - 1) * pl + node
-                                            : (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i));
-            N[i] = (T)PS::load_moving(mv, idx, kScaleN);
-        }
-    }
 
     // isotropic stencils: grad f = 3 sum_i w_i c_i f(x+c_i), lap f = 6 sum_i w_i (f(x+c_i) - f(x)).
     // FP32 sums over +/- pairs (half the multiply-adds); FP64, the mode checked
@@ -655,13 +669,23 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     }
 }
 
-// Halo load, barrier, then every thread's node of the tile at (x0, y0, z0).
+// The tile at (x0, y0, z0): the halo copies are issued first, then every
+// thread pulls its node's populations while they are in flight; after the
+// barrier each fluid node is updated.
 template <int Q, int V, typename T, typename S, bool CONTRAST>
 __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuffers<T, S>& b, T* s_phi, T* s_u,
                                           int x0, int y0, int z0) {
     load_halo<Q, V, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    const bool in_grid = x < P.nx && y < P.ny && z < P.nz;
+    const int node = in_grid ? x + P.nx * (y + P.ny * z) : 0;
+    const uint32_t m = in_grid ? __ldg(b.mask + node) : MASK_NOT_FLUID;
+    const bool fluid = !(m & MASK_NOT_FLUID);
+    T N[Q];
+    if (fluid) pull_node<Q, T, S>(P, b.Nin, m, node, x, y, z, N);
+    cp_async_wait_all();
     __syncthreads();
-    step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, x0 + threadIdx.x, y0 + threadIdx.y, z0 + threadIdx.z);
+    if (fluid) step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, N, node);
 }
 
 template <int Q, typename T, typename S, bool CONTRAST, int V = 0>
