@@ -688,8 +688,17 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
     if (fluid) step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, N, node);
 }
 
+// Resident blocks per SM the step kernels are compiled for (registers per
+// thread <= 65536 / (256 * blocks)): measured on the 192^3 bench case, FP32
+// runs best at 5 (48 registers, no spills), FP16 storage at 6 (40 registers);
+// FP64 keeps the compiler's choice.
+template <typename T, typename S> struct StepOccupancy { static constexpr int kBlocks = 1; };
+template <> struct StepOccupancy<float, float> { static constexpr int kBlocks = 5; };
+template <> struct StepOccupancy<float, __half> { static constexpr int kBlocks = 6; };
+
 template <int Q, typename T, typename S, bool CONTRAST, int V = 0>
-__global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_step(StepParams<T> P, StepBuffers<T, S> b) {
+__global__ void __launch_bounds__(Tile<Q, V>::THREADS, (StepOccupancy<T, S>::kBlocks))
+    k_step(StepParams<T> P, StepBuffers<T, S> b) {
     using Tl = Tile<Q, V>;
     __shared__ T s_phi[Tl::HN];
     __shared__ T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
@@ -719,7 +728,8 @@ template <typename T, typename S>
 __constant__ BatchEntry<T, S> c_batch[kBatchSlots];
 
 template <int Q, typename T, typename S, int V, bool CONTRAST>
-__global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_step_batched(const int4* __restrict__ tiles, int parity) {
+__global__ void __launch_bounds__(Tile<Q, V>::THREADS, (StepOccupancy<T, S>::kBlocks))
+    k_step_batched(const int4* __restrict__ tiles, int parity) {
     using Tl = Tile<Q, V>;
     __shared__ T s_phi[Tl::HN];
     __shared__ T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
