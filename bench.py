@@ -131,7 +131,7 @@ def hbm_peak():
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for name in ("lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_launch.cuh"):
+    for name in ("lbm_kernels.cuh", "lbm_lattice.cuh", "lbm_launch.cuh", "lbm_launch_impl.cuh"):
         with open(os.path.join(ROOT, "paper_2605_30878_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
