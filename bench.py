@@ -167,6 +167,23 @@ def workload(theta, precision, n=N_GRID):
                             mu_ratio=100.0, sigma=0.005, precision=precision)
 
 
+def max_over_ranks(value, dist=None, device="cuda"):
+    """The largest `value` over all ranks (the slowest rank's time); value itself
+    without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, ms_max):
+    """Whole-job throughput of `world` replicas, each advancing nodes_per_rank
+    nodes `steps` steps, timed by the slowest rank."""
+    return nodes_per_rank * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -476,11 +493,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms = start.elapsed_time(end)
     dom.sync()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = nn * args.steps * world / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist)
+    value = whole_job_mlups(nn, args.steps, world, ms)
     diag32 = dom.diagnostics(probe)
 
     # dominant kernel timed kernel by kernel with CUDA events on the same stream
