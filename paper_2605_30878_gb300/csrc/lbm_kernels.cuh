@@ -426,6 +426,34 @@ __device__ __forceinline__ void pull_node(const StepParams<T>& P, const S* __res
     }
 }
 
+// The same pull issued before the node's mask is known: every direction by
+// streaming (x - c_i always lies in the grid), then the directions whose
+// neighbour is not fluid are read again from the node's own opposite slot.
+template <int Q, typename T, typename S>
+__device__ __forceinline__ void pull_streaming(const StepParams<T>& P, const S* __restrict__ Nin, int node, int x,
+                                               int y, int z, T (&N)[Q]) {
+    using L = Lattice<Q>;
+    using PS = PopStore<S>;
+    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz);
+    const int pl = (int)P.plane;
+    N[0] = (T)PS::load_rest(PS::rest(Nin), node);
+    const auto* mv = PS::moving(Nin, pl);
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        N[i] = (T)PS::load_moving(mv, (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i)), kScaleN);
+}
+template <int Q, typename T, typename S>
+__device__ __forceinline__ void pull_bounce_back(const StepParams<T>& P, const S* __restrict__ Nin, uint32_t m,
+                                                 int node, T (&N)[Q]) {
+    using L = Lattice<Q>;
+    using PS = PopStore<S>;
+    const int pl = (int)P.plane;
+    const auto* mv = PS::moving(Nin, pl);
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        if ((m >> i) & 1u) N[i] = (T)PS::load_moving(mv, (L::opp(i) - 1) * pl + node, kScaleN);
+}
+
 // One fluid node of the step: pulled populations N, the block's halo tile.
 template <int Q, int V, typename T, typename S, bool CONTRAST>
 __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuffers<T, S>& b,
@@ -680,9 +708,10 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
     const bool in_grid = x < P.nx && y < P.ny && z < P.nz;
     const int node = in_grid ? x + P.nx * (y + P.ny * z) : 0;
     const uint32_t m = in_grid ? __ldg(b.mask + node) : MASK_NOT_FLUID;
-    const bool fluid = !(m & MASK_NOT_FLUID);
     T N[Q];
-    if (fluid) pull_node<Q, T, S>(P, b.Nin, m, node, x, y, z, N);
+    if (in_grid) pull_streaming<Q, T, S>(P, b.Nin, node, x, y, z, N);      // in flight with the mask load
+    const bool fluid = !(m & MASK_NOT_FLUID);
+    if (fluid && (m & ~MASK_NOT_FLUID)) pull_bounce_back<Q, T, S>(P, b.Nin, m, node, N);
     cp_async_wait_all();
     __syncthreads();
     if (fluid) step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, N, node);
