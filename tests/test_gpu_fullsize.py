@@ -1,0 +1,74 @@
+"""Parity at the bench's full size: the D3Q19 192^3 drop on a sphere (density
+ratio 1000), stepped by the same CUDA graphs the bench times, against the FP64
+oracle on sampled nodes.  The oracle takes the GPU's state after a few steps
+and computes one step at the sampled nodes only (orc_step_sample); the GPU
+advances the same step; the two must agree within the precision's tolerance.
+Samples: random fluid nodes, fluid nodes next to the sphere (bounce-back),
+interface nodes (0.05 < phi < 0.95) and ghost nodes (their updated color)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_30878_gb300 import lbm
+from paper_2605_30878_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lbm.FP64: 1e-12, lbm.FP32: 1e-4, lbm.FP16: 2e-3}
+FLOOR = {"N": 0.0, "B": 0.0, "phi": 0.0, "u": 1.0, "p": 1.0}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_30878_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def _samples(cfg, phi, rng):
+    solid = cfg["solid"].reshape(-1)
+    fluid = np.flatnonzero(solid == 0)
+    # fluid nodes with a solid stencil neighbour: the fluid side of the wall
+    wall = wl.ghost_mask((cfg["solid"] == 0).astype(np.uint8), 19).reshape(-1) & (solid == 0)
+    inter = np.flatnonzero((solid == 0) & (phi > 0.05) & (phi < 0.95))
+    pick = lambda a, k: rng.choice(a, min(k, len(a)), replace=False) if len(a) else a  # noqa: E731
+    return np.unique(np.concatenate([pick(fluid, 1500), pick(np.flatnonzero(wall), 300), pick(inter, 300),
+                                     pick(cfg["ghosts"][0], 200)]))
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.FP16])
+def test_bench_case_step_on_sampled_nodes(precision):
+    cfg = wl.sphere_config(n=192, R=32.0, R0=24.0, theta_deg=60.0, rho_ratio=1000.0, mu_ratio=100.0,
+                           precision=precision)
+    g = lbm.Domain(cfg["params"], cfg["solid"], cfg["ghosts"])
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    g.step(16)                                   # the 8-step graph, as the bench runs it
+    state = {f: g.read(f) for f in ("N", "B", "phi", "u", "p")}
+    rng = np.random.default_rng(11)
+    nodes = _samples(cfg, state["phi"], rng)
+    o = oracle.Oracle(dict(cfg["params"], precision=0), cfg["solid"], cfg["ghosts"])
+    for f, v in state.items():
+        o.set(f, v)
+    want = o.step_sample(nodes)
+    del o, state
+    g.step(1)
+    solid = cfg["solid"].reshape(-1)[nodes]
+    fl = solid == 0
+    ghost = np.isin(nodes, cfg["ghosts"][0])
+    got = {"N": g.read("N")[:, nodes].T, "B": g.read("B")[:, nodes].T, "u": g.read("u")[:, nodes].T,
+           "p": g.read("p")[nodes], "phi": g.read("phi")[nodes]}
+    err = {}
+    for f in ("N", "B", "u", "p"):
+        a, b = got[f][fl], want[f][fl]
+        err[f] = np.abs(a - b).max() / max(np.abs(b).max(), FLOOR[f])
+    # phi after the step at fluid nodes, and the ghost color of the step's opening ghost update
+    # (the GPU's phi array holds the ghost values of the step just taken)
+    a, b = got["phi"][fl], want["phi"][fl]
+    err["phi"] = np.abs(a - b).max() / np.abs(b).max()
+    err["phi_ghost"] = np.abs(got["phi"][ghost] - want["phi"][ghost]).max()
+    print("192^3 sampled parity", precision, len(nodes), {k: "%.2e" % v for k, v in err.items()})
+    assert all(v <= TOL[precision] for v in err.values()), err
+    assert ghost.sum() > 50 and fl.sum() > 1500
