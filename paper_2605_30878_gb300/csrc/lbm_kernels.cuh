@@ -78,11 +78,17 @@ template <typename V> struct PlainStore {
     __device__ static V load_moving(const V* m, int idx, float) { return __ldg(m + idx); }
     __device__ static void store_rest(V* r, int idx, V v) { r[idx] = v; }
     __device__ static void store_moving(V* m, int idx, V v, float) { m[idx] = v; }
+    // stores v and returns what storage lost of it (nothing: stored as computed)
+    __device__ static V store_moving_r(V* m, int idx, V v, float) { m[idx] = v; return V(0); }
 };
-template <> struct PopStore<double> : PlainStore<double> { static constexpr bool kShift = false; };
-template <> struct PopStore<float> : PlainStore<float> { static constexpr bool kShift = true; };
+template <> struct PopStore<double> : PlainStore<double> {
+    static constexpr bool kShift = false, kExact = true;
+};
+template <> struct PopStore<float> : PlainStore<float> {
+    static constexpr bool kShift = true, kExact = true;
+};
 template <> struct PopStore<__half> {
-    static constexpr bool kShift = true;
+    static constexpr bool kShift = true, kExact = false;     // moving populations are rounded on store
     static constexpr int kRestBytes = 4, kMovingBytes = 2;
     __device__ static const float* rest(const __half* p) { return reinterpret_cast<const float*>(p); }
     __device__ static float* rest(__half* p) { return reinterpret_cast<float*>(p); }
@@ -95,6 +101,12 @@ template <> struct PopStore<__half> {
     __device__ static void store_rest(float* r, int idx, float v) { r[idx] = v; }
     __device__ static void store_moving(__half* m, int idx, float v, float scale) {
         m[idx] = __float2half_rn(v * scale);
+    }
+    // stores v and returns the part FP16 rounding dropped, v - stored value
+    __device__ static float store_moving_r(__half* m, int idx, float v, float scale) {
+        const __half h = __float2half_rn(v * scale);
+        m[idx] = h;
+        return v - __half2float(h) * (1.0f / scale);
     }
 };
 
@@ -645,12 +657,17 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
     auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
     // rest direction: no forcing, no stress projection, no recoloring (c_0 = 0)
-    {
-        const T nst = (kShift ? T(0) : P.chi[0]) - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
-        const T bst = kShift ? phi * nst + (phi - T(0.5)) * P.chi[0] : phi * nst;
-        PS::store_rest(Nrest, node, nst);
-        PS::store_rest(Brest, node, bst);
+    const T nst0 = (kShift ? T(0) : P.chi[0]) - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
+    const T bst0 = kShift ? phi * nst0 + (phi - T(0.5)) * P.chi[0] : phi * nst0;
+    if constexpr (PS::kExact) {
+        PS::store_rest(Nrest, node, nst0);
+        PS::store_rest(Brest, node, bst0);
     }
+    // What storage drops of the moving populations (FP16 rounding) is added to
+    // the node's rest population, kept in float: the stored N* and B* of a node
+    // then sum to what the collision and segregation produced, so storage
+    // rounding moves no mass between phases or out of the domain.
+    T lostN = T(0), lostB = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
@@ -677,18 +694,22 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
             const T odd = wi * (cu3 + halfF * cF);
             const T ni = even + odd, no = even - odd;
             const T shift_b = kShift ? (phi - T(0.5)) * P.chi[i] : T(0);
-            PS::store_moving(Nmov, (i - 1) * pl + node, ni, kScaleN);
-            PS::store_moving(Nmov, (o - 1) * pl + node, no, kScaleN);
-            PS::store_moving(Bmov, (i - 1) * pl + node, phi * ni + shift_b + rc, kScaleB);
-            PS::store_moving(Bmov, (o - 1) * pl + node, phi * no + shift_b - rc, kScaleB);
+            lostN += PS::store_moving_r(Nmov, (i - 1) * pl + node, ni, kScaleN);
+            lostN += PS::store_moving_r(Nmov, (o - 1) * pl + node, no, kScaleN);
+            lostB += PS::store_moving_r(Bmov, (i - 1) * pl + node, phi * ni + shift_b + rc, kScaleB);
+            lostB += PS::store_moving_r(Bmov, (o - 1) * pl + node, phi * no + shift_b - rc, kScaleB);
         } else {
             const T neq = chi_i + wi * (common + cu3 + T(0.5) * cu3 * cu3);
             const T nst = neq + wi * halfF * cF + proj;
             // B* = phi N* + recolor; stored as B* - chi_i/2 = phi dN* + (phi - 1/2) chi_i + recolor
             const T bst = (kShift ? phi * nst + (phi - T(0.5)) * P.chi[i] : phi * nst) + rc;
-            PS::store_moving(Nmov, (i - 1) * pl + node, nst, kScaleN);
-            PS::store_moving(Bmov, (i - 1) * pl + node, bst, kScaleB);
+            lostN += PS::store_moving_r(Nmov, (i - 1) * pl + node, nst, kScaleN);
+            lostB += PS::store_moving_r(Bmov, (i - 1) * pl + node, bst, kScaleB);
         }
+    }
+    if constexpr (!PS::kExact) {
+        PS::store_rest(Nrest, node, nst0 + lostN);
+        PS::store_rest(Brest, node, bst0 + lostB);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
