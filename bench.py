@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--serve-plain", action="store_true",
                     help="also serve the same stream with per-case launches instead of batches")
     ap.add_argument("--no-table", action="store_true", help="skip the paper's Table I grids")
+    ap.add_argument("--no-other-storage", action="store_true",
+                    help="skip the run of the same case with the other population storage (fp16 / fp32)")
     ap.add_argument("--table-steps", type=int, default=2000)
     ap.add_argument("--packing-steps", type=int, default=0,
                     help="run the 256^3 sphere-packing imbibition for this many steps in FP64, FP32 and "
@@ -330,6 +332,37 @@ def time_domain(dom, steps, warmup=20):
     return e0.elapsed_time(e1) * 1e-3 / steps
 
 
+def run_other_storage(lbm, args, cfg, probe, n_angle, fp64_deg):
+    """The bench case with the other population storage: ms per step (CUDA
+    events, same K and W), its k_step against its own algorithmic bytes, and
+    its contact angle after n_angle steps against FP64's."""
+    import torch
+    prec = lbm.FP32 if args.storage == "fp16" else lbm.FP16
+    key = "fp32" if prec == lbm.FP32 else "fp16"
+    P = dict(cfg["params"], precision=prec)
+    d = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
+    fluid = d.fluid_nodes()
+    d.init_droplet(cfg["drop_center"], cfg["R0"])
+    sec = time_domain(d, args.steps, warmup=args.warmup)
+    kms = d.profile_steps(max(3, min(args.steps, 60)))
+    t_step = kms[1] / max(3, min(args.steps, 60)) * 1e-3
+    pop = 4 + 2 * 18 if prec == lbm.FP16 else 19 * 4
+    kb = k_step_bytes_per_fluid_node(19, 3, 4, True, pop) * fluid
+    peak, peak_kind = hbm_peak()
+    d.close()
+    da = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
+    da.init_droplet(cfg["drop_center"], cfg["R0"])
+    da.step(n_angle)
+    deg = math.degrees(da.diagnostics(probe)["contact_angle"])
+    da.close()
+    torch.cuda.empty_cache()
+    n = cfg["params"]["nx"]
+    return {"storage": key, "value": n ** 3 / sec / 1e6, "unit": "MLUPS", "ms_per_step": sec * 1e3,
+            "k_step": {"avg_launch_ms": t_step * 1e3, "bytes_per_fluid_node": kb / fluid,
+                       "achieved_gbs": kb / t_step / 1e9, "frac": kb / t_step / 1e9 / peak, "peak_kind": peak_kind},
+            "contact_angle_deg": deg, "vs_fp64_deg": abs(deg - fp64_deg) if fp64_deg is not None else None}
+
+
 def run_paper_table(lbm, steps):
     """The paper's Table I grids of its two static wetting benchmarks (drop on
     a flat plate: walls at y = 0 and y = ny-1, periodic x, drop area 1e4 at
@@ -547,10 +580,18 @@ def run_ours(args):
         h2d = nn + ng * (4 + 8 * 4 + 8 * s)
         d2h = 32 * 8 + 4
 
+        # the other storage precision on the same case (FP16 storage when the line is FP32 and back)
+        other = None
+        if world == 1 and not args.no_other_storage:
+            try:
+                other = run_other_storage(lbm, args, cfg, probe, n_angle, angle.get("fp64_deg"))
+            except Exception as exc:
+                other = {"error": repr(exc)}
+
         note("cpu")
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            rate, st, dt = time_oracle(cfg, 10.0, 6)
+            rate, st, dt = time_oracle(cfg, 10.0, 20)
             cpu = {"value": rate, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
                    "sample": "%d FP64 oracle steps of the %d^3 workload after 1 warm-up step (%.1f s)" % (st, n, dt)}
 
@@ -611,6 +652,7 @@ def run_ours(args):
             "gpu_launches": launches * args.steps,
             "clocks": clk,
             "contact_angle": angle,
+            "other_storage": other,
             "batched": batched,
             "serving": serving,
             "paper_table1": table,

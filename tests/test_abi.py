@@ -66,6 +66,12 @@ def test_domain_bytes(L):
     assert lbm.domain_bytes(dict(cfg["params"], lattice=7), ng) == 0
     assert lbm.domain_bytes(dict(cfg["params"], lattice=9), ng) == 0          # D2Q9 needs nz == 1
     assert lbm.domain_bytes(cfg["params"], -1) == 0
+    # the largest grids: populations are indexed in 32 bits, Q * plane < 2^31
+    big = dict(cfg["params"], nx=480, ny=480, nz=480)
+    assert lbm.domain_bytes(big, 0) > 19 * 4 * 4 * 480 ** 3        # 110.6M nodes: accepted
+    assert lbm.domain_bytes(dict(big, nx=512, ny=512, nz=512), 0) == 0
+    assert lbm.domain_bytes(dict(cfg["params"], lattice=9, nx=16000, ny=16000, nz=1), 0) == 0      # 9 x 256M
+    assert lbm.domain_bytes(dict(cfg["params"], lattice=9, nx=15000, ny=15000, nz=1), 0) > 0       # 9 x 225M
 
 
 def _create_error(params, solid, ghosts):
