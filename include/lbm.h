@@ -257,13 +257,21 @@ lbm_status lbm_batch_step(lbm_batch* b, int64_t n);
 /* Wait for the batch stream; LBM_ERR_UNSTABLE if any domain went non-finite. */
 lbm_status lbm_batch_sync(lbm_batch* b);
 
-/* Autotuner: time steps_per_trial batched steps with each of the three block
- * tile shapes (D3Q19: 32x4x2, 32x2x4, 32x8x1; D2Q9: 32x8, 64x4, 128x2), keep the
- * fastest; ms_per_step[3] (may be NULL) receives the timings.  Tuning advances
- * every domain by 3 (steps_per_trial + 1) steps and synchronises. */
+/* Block tile shapes of the batched step kernels (shape 0 is the single-domain
+ * kernels' tile):
+ *            0        1        2        3        4
+ *   D3Q19  32x4x2   32x2x4   32x8x1   32x2x2   32x4x4
+ *   D2Q9   32x8     64x4     128x2    32x4     32x16
+ *   threads 256      256      256      128      512 */
+enum { LBM_BATCH_TILE_SHAPES = 5 };
+
+/* Autotuner: time steps_per_trial batched steps with each tile shape and block
+ * size above, keep the fastest; ms_per_step[LBM_BATCH_TILE_SHAPES] (may be
+ * NULL) receives the timings.  Tuning advances every domain by
+ * LBM_BATCH_TILE_SHAPES * (steps_per_trial + 1) steps and synchronises. */
 lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_trial, int32_t* chosen, double* ms_per_step);
 
-/* Current tile shape of the batch, or set one directly (0, 1, 2). */
+/* Current tile shape of the batch, or set one directly (0 .. LBM_BATCH_TILE_SHAPES-1). */
 int32_t lbm_batch_variant(const lbm_batch* b);
 lbm_status lbm_batch_set_variant(lbm_batch* b, int32_t variant);
 

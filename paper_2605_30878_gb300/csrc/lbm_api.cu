@@ -16,6 +16,8 @@
 
 using namespace lbmgpu;
 
+static_assert(kTileVariants == LBM_BATCH_TILE_SHAPES, "tile shapes of the kernels and of the header");
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -783,12 +785,12 @@ struct lbm_batch {
     std::vector<int> cur0;             // each domain's buffer parity when the batch was made
     int parity = 0;                    // steps taken by the batch, mod 2
     int variant = 0;
-    int ntiles[kTileVariants] = {0, 0, 0};
-    int ncontrast[kTileVariants] = {0, 0, 0};   // tiles of domains with density contrast come first
+    int ntiles[kTileVariants] = {};
+    int ncontrast[kTileVariants] = {};           // tiles of domains with density contrast come first
     int device = 0;
     std::vector<int> slots;            // each domain's slot of the constant table
     char* dev = nullptr;               // one allocation for every device table
-    int4* tiles[kTileVariants] = {nullptr, nullptr, nullptr};   // {slot, x0, y0, z0}
+    int4* tiles[kTileVariants] = {};             // {slot, x0, y0, z0}
     void* ghost_tabs = nullptr;
     int64_t* ghost_begin = nullptr;
     int64_t total_ghosts = 0;
@@ -843,9 +845,7 @@ void bdispatch(int precision, F&& f) {
 // Appends the tiles {slot, x0, y0, z0} of a domain for tile shape V (the
 // shapes of Tile<Q, V>).
 void append_tiles(int Q, int V, const lbm_params& P, int i, std::vector<int4>& out) {
-    int TX, TY, TZ;
-    if (Q == 9) { TX = V == 0 ? 32 : (V == 1 ? 64 : 128); TY = V == 0 ? 8 : (V == 1 ? 4 : 2); TZ = 1; }
-    else { TX = 32; TY = V == 0 ? 4 : (V == 1 ? 2 : 8); TZ = V == 0 ? 2 : (V == 1 ? 4 : 1); }
+    const int TX = tile_extent(Q, V, 0), TY = tile_extent(Q, V, 1), TZ = tile_extent(Q, V, 2);
     for (int z = 0; z < P.nz; z += TZ)
         for (int y = 0; y < P.ny; y += TY)
             for (int x = 0; x < P.nx; x += TX) out.push_back(make_int4(i, x, y, z));
@@ -869,7 +869,13 @@ lbm_status batch_capture(lbm_batch* b) {
         if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, cudaGetErrorString(e));
         if (k < 2) batch_launch_step(b, k, b->cap);
         else for (int t = 0; t < 8; ++t) batch_launch_step(b, t & 1, b->cap);
+        const cudaError_t le = cudaGetLastError();          // a launch the capture refused
         e = cudaStreamEndCapture(b->cap, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return bfail(b, LBM_ERR_CUDA, std::string("batch launch (tile shape ") + std::to_string(b->variant) +
+                                              "): " + cudaGetErrorString(le));
+        }
         if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
         cudaGraphExec_t* dst = k == 0 ? &b->g1[0] : (k == 1 ? &b->g1[1] : &b->g8);
         e = cudaGraphInstantiate(dst, g, 0);
@@ -1037,6 +1043,13 @@ lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_trial, int32_t* chosen
         b->variant = V;
         batch_launch_step(b, b->parity, b->stream);        // warm-up step of this shape
         b->parity ^= 1;
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return bfail(b, LBM_ERR_CUDA, std::string("batch launch (tile shape ") + std::to_string(V) +
+                                              "): " + cudaGetErrorString(le));
+        }
         cudaEventRecord(e0, b->stream);
         for (int t = 0; t < steps_per_trial; ++t) {
             batch_launch_step(b, b->parity, b->stream);
@@ -1063,7 +1076,7 @@ lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_trial, int32_t* chosen
 int32_t lbm_batch_variant(const lbm_batch* b) { return b ? b->variant : -1; }
 
 lbm_status lbm_batch_set_variant(lbm_batch* b, int32_t v) {
-    if (!b || v < 0 || v >= kTileVariants) return bfail(b, LBM_ERR_ARG, "variant must be 0, 1 or 2");
+    if (!b || v < 0 || v >= kTileVariants) return bfail(b, LBM_ERR_ARG, "variant must be in 0.." + std::to_string(kTileVariants - 1));
     b->variant = v;
     return batch_capture(b);
 }

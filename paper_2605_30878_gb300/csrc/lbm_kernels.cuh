@@ -142,15 +142,26 @@ struct StepBuffers {
 // so the pull in direction i bounces back; MASK_NOT_FLUID marks non-fluid x.
 constexpr uint32_t MASK_NOT_FLUID = 0x80000000u;
 
-// Block tile of the step kernels: 256 threads, one node each, in one of three
-// shapes (V = 0, 1, 2) that the batch autotuner chooses between.
-//   D3Q19: 32x4x2, 32x2x4, 32x8x1      D2Q9: 32x8, 64x4, 128x2
+// Block tiles of the step kernels, one node per thread, in the shapes the
+// batch autotuner chooses between (V = 0 is the single-domain kernels' tile):
+//   V        0        1        2        3        4
+//   D3Q19  32x4x2   32x2x4   32x8x1   32x2x2   32x4x4
+//   D2Q9   32x8     64x4     128x2    32x4     32x16
+//   threads  256      256      256      128      512
+constexpr int kTileVariants = 5;
+__host__ __device__ constexpr int tile_extent(int Q, int V, int axis) {
+    return Q == 9 ? (axis == 0 ? (V == 1 ? 64 : (V == 2 ? 128 : 32))
+                               : axis == 1 ? (V == 0 ? 8 : (V == 1 ? 4 : (V == 2 ? 2 : (V == 3 ? 4 : 16)))) : 1)
+                  : (axis == 0 ? 32
+                               : axis == 1 ? (V == 0 ? 4 : (V == 1 ? 2 : (V == 2 ? 8 : (V == 3 ? 2 : 4))))
+                                           : (V == 0 ? 2 : (V == 1 ? 4 : (V == 2 ? 1 : (V == 3 ? 2 : 4)))));
+}
 template <int Q, int V = 0>
 struct Tile {
     static constexpr int D = Lattice<Q>::D;
-    static constexpr int TX = (D == 2) ? (V == 0 ? 32 : (V == 1 ? 64 : 128)) : 32;
-    static constexpr int TY = (D == 2) ? (V == 0 ? 8 : (V == 1 ? 4 : 2)) : (V == 0 ? 4 : (V == 1 ? 2 : 8));
-    static constexpr int TZ = (D == 2) ? 1 : (V == 0 ? 2 : (V == 1 ? 4 : 1));
+    static constexpr int TX = tile_extent(Q, V, 0);
+    static constexpr int TY = tile_extent(Q, V, 1);
+    static constexpr int TZ = tile_extent(Q, V, 2);
     static constexpr int HX = TX + 2;
     static constexpr int HY = TY + 2;
     static constexpr int HZ = (D == 2) ? 1 : TZ + 2;
@@ -159,7 +170,6 @@ struct Tile {
     // offset of the halo slot of x + c in a halo tile
     __host__ __device__ static constexpr int off(int cx, int cy, int cz) { return cx + HX * (cy + HY * cz); }
 };
-constexpr int kTileVariants = 3;
 
 __device__ __forceinline__ int wrap_any(int v, int n) {
     v %= n;
@@ -745,9 +755,14 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
 template <typename T, typename S> struct StepOccupancy { static constexpr int kBlocks = 1; };
 template <> struct StepOccupancy<float, float> { static constexpr int kBlocks = 5; };
 template <> struct StepOccupancy<float, __half> { static constexpr int kBlocks = 6; };
+// the same register budget for other block sizes
+template <typename T, typename S, int THREADS>
+constexpr int step_min_blocks() {
+    return StepOccupancy<T, S>::kBlocks * 256 / THREADS > 0 ? StepOccupancy<T, S>::kBlocks * 256 / THREADS : 1;
+}
 
 template <int Q, typename T, typename S, bool CONTRAST, int V = 0>
-__global__ void __launch_bounds__(Tile<Q, V>::THREADS, (StepOccupancy<T, S>::kBlocks))
+__global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Tile<Q, V>::THREADS>()))
     k_step(StepParams<T> P, StepBuffers<T, S> b) {
     using Tl = Tile<Q, V>;
     __shared__ T s_phi[Tl::HN];
@@ -778,7 +793,7 @@ template <typename T, typename S>
 __constant__ BatchEntry<T, S> c_batch[kBatchSlots];
 
 template <int Q, typename T, typename S, int V, bool CONTRAST>
-__global__ void __launch_bounds__(Tile<Q, V>::THREADS, (StepOccupancy<T, S>::kBlocks))
+__global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Tile<Q, V>::THREADS>()))
     k_step_batched(const int4* __restrict__ tiles, int parity) {
     using Tl = Tile<Q, V>;
     __shared__ T s_phi[Tl::HN];

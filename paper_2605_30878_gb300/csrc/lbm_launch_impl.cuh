@@ -168,10 +168,14 @@ void Launch<T, S>::step_phi_batched(int Q, int V, const int4* tiles, int ntiles,
         if (V == 0) step_batched_v<9, 0>(tiles, ntiles, ncontrast, parity, s);
         if (V == 1) step_batched_v<9, 1>(tiles, ntiles, ncontrast, parity, s);
         if (V == 2) step_batched_v<9, 2>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 3) step_batched_v<9, 3>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 4) step_batched_v<9, 4>(tiles, ntiles, ncontrast, parity, s);
     } else {
         if (V == 0) step_batched_v<19, 0>(tiles, ntiles, ncontrast, parity, s);
         if (V == 1) step_batched_v<19, 1>(tiles, ntiles, ncontrast, parity, s);
         if (V == 2) step_batched_v<19, 2>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 3) step_batched_v<19, 3>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 4) step_batched_v<19, 4>(tiles, ntiles, ncontrast, parity, s);
     }
 }
 

@@ -18,6 +18,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOU
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_UNSTABLE",
                 -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_UNSUPPORTED"}
 FP64, FP32, FP16 = 0, 1, 2     # FP16: FP32 arithmetic, FP16 population storage
+BATCH_TILE_SHAPES = 5          # LBM_BATCH_TILE_SHAPES: tile shapes / block sizes of the batched kernels
 GHOST_PRESENT, GHOST_FAKHARI = 0, 1
 FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 
@@ -381,7 +382,7 @@ class Batch:
     def tune(self, steps_per_trial=20):
         """Time every tile shape, keep the fastest; returns (chosen, ms per step of each)."""
         ch = C.c_int32()
-        ms = np.zeros(3)
+        ms = np.zeros(BATCH_TILE_SHAPES)
         self._check(load().lbm_batch_tune(self.h, int(steps_per_trial), C.byref(ch), ms.ctypes.data_as(_dp)))
         return ch.value, ms
 

@@ -52,16 +52,13 @@ def test_batch_equals_individual_steps(precision):
     cfgs = _cases(precision)
     alone = _make(cfgs)
     for d in alone:
-        d.step(12)                        # 5 + 4 + 3 batched steps
+        d.step(16)                        # 5 + 4 + 3 + 2 + 2 batched steps
     mixed = _make(cfgs)
     mixed[1].step(1)                      # domains may enter the batch at different parities
     b = lbm.Batch(mixed)
-    b.set_variant(1)
-    b.step(5)
-    b.set_variant(2)
-    b.step(4)
-    b.set_variant(0)
-    b.step(3)
+    for v, n in ((1, 5), (2, 4), (0, 3), (3, 2), (4, 2)):
+        b.set_variant(v)
+        b.step(n)
     b.sync()
     alone[1].step(1)                      # the extra step domain 1 took before joining
     for k, (a, m) in enumerate(zip(alone, mixed)):
@@ -86,9 +83,10 @@ def test_autotuner_picks_a_shape_and_keeps_results():
     a, m = _make(cfgs), _make(cfgs)
     b = lbm.Batch(m)
     chosen, ms = b.tune(steps_per_trial=3)
-    assert chosen in (0, 1, 2) and (ms > 0).all() and b.variant == chosen
+    assert chosen in range(lbm.BATCH_TILE_SHAPES) and len(ms) == lbm.BATCH_TILE_SHAPES and (ms > 0).all()
+    assert b.variant == chosen
     for d in a:
-        d.step(12)                        # tuning advanced every domain 3 x (3 + 1) steps
+        d.step(4 * lbm.BATCH_TILE_SHAPES)   # tuning advanced every domain shapes x (3 + 1) steps
     b.sync()
     for x, y in zip(a, m):
         assert np.array_equal(x.read("B"), y.read("B"))
@@ -115,10 +113,10 @@ def test_batch_equals_individual_steps_d2q9(precision):
     cfgs = _cases_2d(precision)
     alone, mixed = _make(cfgs), _make(cfgs)
     for d in alone:
-        d.step(11)
+        d.step(15)
     b = lbm.Batch(mixed)
     assert b.launches_per_step() == 4            # ghosts, contrast step, plain step, color
-    for v, n in ((2, 3), (1, 3), (0, 5)):
+    for v, n in ((2, 3), (1, 3), (0, 5), (3, 2), (4, 2)):
         b.set_variant(v)
         b.step(n)
     b.sync()
