@@ -276,8 +276,10 @@ template <int Q, typename T, typename S>
 __global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const S* __restrict__ Bst,
                                                           const uint32_t* __restrict__ mask, T* __restrict__ phi) {
     using Tl = Tile<Q>;
-    phi_node<Q, T, S>(P, Bst, mask, phi, blockIdx.x * Tl::TX + threadIdx.x, blockIdx.y * Tl::TY + threadIdx.y,
-                      blockIdx.z * Tl::TZ + threadIdx.z);
+    // tiles in the reverse of k_step's order: the B* that k_step wrote last is
+    // still in L2 when this kernel starts
+    const int bx = gridDim.x - 1 - blockIdx.x, by = gridDim.y - 1 - blockIdx.y, bz = gridDim.z - 1 - blockIdx.z;
+    phi_node<Q, T, S>(P, Bst, mask, phi, bx * Tl::TX + threadIdx.x, by * Tl::TY + threadIdx.y, bz * Tl::TZ + threadIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -805,7 +807,7 @@ __global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Ti
 
 template <int Q, typename T, typename S, int V>
 __global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_phi_batched(const int4* __restrict__ tiles, int parity) {
-    const int4 t = __ldg(tiles + blockIdx.x);
+    const int4 t = __ldg(tiles + (gridDim.x - 1 - blockIdx.x));     // reverse order, as k_phi
     const BatchEntry<T, S>& e = c_batch<T, S>[t.x];
     // this step's output B* is the buffer the step kernel wrote
     phi_node<Q, T, S>(e.P, e.b[parity].Bout, e.b[parity].mask, e.b[parity].phi, t.y + threadIdx.x, t.z + threadIdx.y,
