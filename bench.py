@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-case batched measurement")
-    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-steps", type=int, default=5000, help="timed steps of config 4 (each arm)")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the served workload (Poisson arrivals at 20/s); 0 skips it")
     ap.add_argument("--serve-plain", action="store_true",
@@ -275,44 +275,67 @@ def batch_cases(seed=2, count=64):
 
 
 def run_batch_bench(lbm, steps):
-    """Aggregate MLUPS of the 64 cases advanced by one batched launch per phase
-    (tile shape autotuned) against the same cases each stepped by its own launches."""
+    """Config 4: aggregate MLUPS of the 64 cases advanced in one batch (one
+    launch per phase, tile shape autotuned) against a second copy of the same
+    cases each stepped by its own launches, for the same number of steps; then
+    the contact angle of every case from both copies."""
     import torch
     cfgs = batch_cases()
-    doms = []
-    for c in cfgs:
-        d = lbm.Domain(c["params"], c["solid"], c["ghosts"])
-        d.init_droplet(c["drop_center"], c["R0"])
-        doms.append(d)
+
+    def make():
+        out = []
+        for c in cfgs:
+            d = lbm.Domain(c["params"], c["solid"], c["ghosts"])
+            d.init_droplet(c["drop_center"], c["R0"])
+            out.append(d)
+        return out
+    plain, batched = make(), make()
     nodes = sum(int((c["solid"] == 0).sum()) for c in cfgs)      # fluid nodes, as the main metric
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    for d in doms:
-        d.step(3)
+    b = lbm.Batch(batched)
+    chosen, trial_ms = b.tune(steps_per_trial=10)                 # advances every case
+    lead = lbm.BATCH_TILE_SHAPES * 11
+    for d in plain:
+        d.step(lead)                                              # the same steps, untimed
     torch.cuda.synchronize()
     ev[0].record(stream)
-    for d in doms:
+    for d in plain:
         d.step(steps)
     ev[1].record(stream)
     torch.cuda.synchronize()
     t_plain = ev[0].elapsed_time(ev[1]) * 1e-3
-    b = lbm.Batch(doms)
-    chosen, trial_ms = b.tune(steps_per_trial=10)
-    torch.cuda.synchronize()
     ev[2].record(stream)
     b.step(steps)
     ev[3].record(stream)
     torch.cuda.synchronize()
     t_batch = ev[2].elapsed_time(ev[3]) * 1e-3
     b.sync()
-    res = {"cases": len(cfgs), "nodes": nodes, "steps": steps,
+    dtheta, err_set = [], []
+    for c, dp, db in zip(cfgs, plain, batched):
+        probe = lbm.make_probe(1, c["solid_center"], c["R"], (0, 0, 1), 6.0)
+        tp = math.degrees(dp.diagnostics(probe)["contact_angle"])
+        tb = math.degrees(db.diagnostics(probe)["contact_angle"])
+        if math.isnan(tp) and math.isnan(tb):
+            dtheta.append(0.0)                                    # no fit on either copy
+        elif math.isnan(tp) or math.isnan(tb):
+            dtheta.append(float("inf"))
+        else:
+            dtheta.append(abs(tb - tp))
+        if math.isfinite(tb):
+            err_set.append(abs(tb - math.degrees(c["params"]["theta"])))
+    res = {"cases": len(cfgs), "nodes": nodes, "steps": steps, "steps_before_timing": lead,
            "mlups_batched": nodes * steps / t_batch / 1e6, "mlups_plain": nodes * steps / t_plain / 1e6,
            "speedup": t_plain / t_batch, "tile_shape_chosen": int(chosen),
            "tune_ms_per_step": [round(float(x), 4) for x in trial_ms],
            "launches_per_step_batched": b.launches_per_step(),
-           "launches_per_step_plain": sum(d.launches_per_step() for d in doms)}
+           "launches_per_step_plain": sum(d.launches_per_step() for d in plain),
+           "contact_angle_batched_vs_plain_max_deg": max(dtheta),
+           "contact_angle_vs_set_deg": {"median": float(np.median(err_set)) if err_set else None,
+                                        "max": float(np.max(err_set)) if err_set else None,
+                                        "measured": len(err_set)}}
     b.close()
-    for d in doms:
+    for d in plain + batched:
         d.close()
     torch.cuda.empty_cache()
     return res
