@@ -217,6 +217,15 @@ def cores_used():
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
+def arm_config(n, theta, storage, world):
+    """The bench line's `config` (both arms)."""
+    return {"workload": "D3Q19 %d^3 drop on sphere: sphere R=%g at the centre, drop R0=%g on the +z pole "
+                        "at theta=%g deg, rho_l/rho_g=1000, mu_l/mu_g=100, sigma=0.005, %s, periodic"
+                        % (n, R_SPHERE * n / N_GRID, R_DROP * n / N_GRID, theta,
+                           "FP32" if storage == "fp32" else "FP32 arithmetic, FP16 populations"),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: each timed step is one full
     oracle time step of a scaled replica of the workload (same geometry ratios
@@ -247,8 +256,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "D3Q19 192^3 drop on sphere (oracle on a scaled replica)", "grid_ref": n_ref,
-                       "theta_deg": theta, "rho_ratio": 1000.0, "mu_ratio": 100.0, "sigma": 0.005},
+            "config": dict(arm_config(args.n, theta, args.storage, 1), sample_grid=n_ref),
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -653,13 +661,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if sp == 4 else "f32 (f16 population storage)", "data": "synthetic",
-            "config": {"workload": "D3Q19 %d^3 drop on sphere: sphere R=%g at the centre, drop R0=%g on the +z pole "
-                                   "at theta=%g deg, rho_l/rho_g=1000, mu_l/mu_g=100, sigma=0.005, %s, periodic"
-                                   % (n, R_SPHERE * n / N_GRID, R_DROP * n / N_GRID, theta,
-                                      "FP32" if sp == 4 else "FP32 arithmetic, FP16 populations"),
-                       "nodes": nn, "fluid_nodes": fluid, "ghost_nodes": ng,
-                       "l2": "inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (lbm.domain_bytes(P, ng) / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": dict(arm_config(n, theta, args.storage, world), nodes=nn, fluid_nodes=fluid, ghost_nodes=ng,
+                           l2="inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (lbm.domain_bytes(P, ng) / 1e9)),
             "roofline": {"bound": "hbm", "kernel": "k_step<19,float,%s,contrast>" % ("half" if sp == 2 else "float"),
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
