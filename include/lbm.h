@@ -39,7 +39,7 @@ typedef enum {
     LBM_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     LBM_ERR_UNSTABLE = -4,     /* a step produced a non-finite velocity or color */
     LBM_ERR_TIMEOUT = -5,      /* reserved for bounded device waits */
-    LBM_ERR_UNSUPPORTED = -6   /* valid request this build does not implement */
+    LBM_ERR_UNSUPPORTED = -6   /* valid request the library does not implement */
 } lbm_status;
 
 typedef enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 } lbm_lattice;

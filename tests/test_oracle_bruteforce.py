@@ -8,7 +8,7 @@ The formulation follows Appendix A of the paper (Eqs. MRTCOLL,
 equilibriumDistribution, forceGuo, totalForce, pressCorrection,
 viscCorrection, segragationStepBlue, phiUpdate, velUpdate, pressureUpdate,
 propTotal, propBlue), Eq. (surfaceTensionForce), the ghost rule of Eq.
-(ghost-nodePrescription) and this build's readings where the paper is
+(ghost-nodePrescription) and the readings taken where the paper is
 silent: isotropic lattice stencils, halfway bounce-back, the force-free
 pressure in F_p and the previous step's velocity in F_visc, the ghost update
 at the start of the step, n_phi = grad phi / max(|grad phi|, 1e-6).  The
@@ -40,8 +40,8 @@ M = np.array([[1, 1, 1, 1, 1, 1, 1, 1, 1],
 CS2 = 1.0 / 3.0
 OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
 
-# D3Q19 (this build's extension, reading R6): rest, +-x, +-y, +-z, then the
-# twelve edges in +- pairs; w = 1/3, 1/18, 1/36
+# D3Q19 (the model's 3D extension; not in the paper): rest, +-x, +-y, +-z,
+# then the twelve edges in +- pairs; w = 1/3, 1/18, 1/36
 C19 = np.array([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
                 [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
                 [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]])
