@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-other-storage", action="store_true",
                     help="skip the run of the same case with the other population storage (fp16 / fp32)")
     ap.add_argument("--table-steps", type=int, default=2000)
+    ap.add_argument("--sweep-steps", type=int, default=0,
+                    help="contact-angle sweep 30..150 deg of the bench case for this many FP32 steps (0 skips it)")
+    ap.add_argument("--sweep-fp64-steps", type=int, default=2000,
+                    help="steps of the FP32-vs-FP64 comparison within the sweep")
     ap.add_argument("--packing-steps", type=int, default=0,
                     help="run the 256^3 sphere-packing imbibition for this many steps in FP64, FP32 and "
                          "FP16 storage (0 skips it)")
@@ -394,6 +398,35 @@ def run_other_storage(lbm, args, cfg, probe, n_angle, fp64_deg):
             "contact_angle_deg": deg, "vs_fp64_deg": abs(deg - fp64_deg) if fp64_deg is not None else None}
 
 
+def run_theta_sweep(lbm, n, steps, fp64_steps):
+    """Config 2 over its angles: the bench case at theta = 30, 60, 90, 120,
+    150 deg, FP32 for `steps` steps (measured angle, max |u|, MLUPS) and, on
+    the same case, FP32 against FP64 after `fp64_steps` steps."""
+    import torch
+    out = {"steps": steps, "fp64_steps": fp64_steps, "angles": []}
+    for theta in (30.0, 60.0, 90.0, 120.0, 150.0):
+        cfg = workload(theta, lbm.FP32, n=n)
+        probe = lbm.make_probe(1, (n / 2.0, n / 2.0, n / 2.0), R_SPHERE * n / N_GRID, (0, 0, 1), 6.0)
+        row = {"theta_set_deg": theta}
+        deg = {}
+        for prec, key in ((lbm.FP32, "fp32"), (lbm.FP64, "fp64")):
+            d = lbm.Domain(dict(cfg["params"], precision=prec), cfg["solid"], cfg["ghosts"])
+            d.init_droplet(cfg["drop_center"], cfg["R0"])
+            d.step(fp64_steps)
+            deg[key] = math.degrees(d.diagnostics(probe)["contact_angle"])
+            if prec == lbm.FP32:
+                sec = time_domain(d, steps - fp64_steps, warmup=0)
+                dg = d.diagnostics(probe)
+                row.update(theta_fp32_deg=math.degrees(dg["contact_angle"]), max_u=dg["max_u"],
+                           mlups=n ** 3 / sec / 1e6, nan_flag=dg["nan_flag"])
+            d.close()
+            torch.cuda.empty_cache()
+        row["fp32_vs_fp64_deg_at_fp64_steps"] = abs(deg["fp32"] - deg["fp64"])
+        out["angles"].append(row)
+        print("sweep", row, file=sys.stderr, flush=True)
+    return out
+
+
 def run_paper_table(lbm, steps):
     """The paper's Table I grids of its two static wetting benchmarks (drop on
     a flat plate: walls at y = 0 and y = ny-1, periodic x, drop area 1e4 at
@@ -641,6 +674,12 @@ def run_ours(args):
             except Exception as exc:
                 table = {"error": repr(exc)}
         note("packing")
+        sweep = None
+        if world == 1 and args.sweep_steps > 0:
+            try:
+                sweep = run_theta_sweep(lbm, n, args.sweep_steps, min(args.sweep_fp64_steps, args.sweep_steps))
+            except Exception as exc:
+                sweep = {"error": repr(exc)}
         packing = None
         if world == 1 and args.packing_steps > 0:
             try:
@@ -683,6 +722,7 @@ def run_ours(args):
             "serving": serving,
             "paper_table1": table,
             "packing": packing,
+            "theta_sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
