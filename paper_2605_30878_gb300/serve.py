@@ -121,7 +121,10 @@ class GpuBackend:
         return case
 
     def open(self, req, case):
-        d = self.lbm.Domain(case["params"], case["solid"], case["ghosts"], stream=self.streams[req.lattice])
+        # the workspace is allocated on the stream that will use it, so the
+        # caching allocator orders its reuse after that stream's work
+        with self.torch.cuda.stream(self.streams[req.lattice]):
+            d = self.lbm.Domain(case["params"], case["solid"], case["ghosts"], stream=self.streams[req.lattice])
         d.init_droplet(case["drop_center"], case["R0"])
         probe = self.lbm.make_probe(1, case["solid_center"], case["R"], case["normal"],
                                     min(self.exclude, 0.5 * case["cap_height"]))
