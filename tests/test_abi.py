@@ -115,3 +115,12 @@ def test_ghost_records_have_the_lbm_ghost_layout():
     assert g[1].node == 7 and list(g[1].n) == [0.0, 0.6, 0.8]
     empty, n0 = lbm.ghost_array(np.zeros(0, np.int64), np.zeros((0, 3)))
     assert n0 == 0 and len(empty) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No CPU fallback: without the compiled library the binding raises."""
+    from paper_2605_30878_gb300 import lbm as binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", "/nonexistent/liblbm.so")
+    with pytest.raises(RuntimeError, match="missing"):
+        binding.load()
