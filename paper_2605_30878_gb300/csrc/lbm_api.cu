@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm.h"
@@ -105,6 +106,10 @@ struct lbm_domain {
     cudaGraphExec_t g1[2] = {nullptr, nullptr};
     cudaGraphExec_t g8 = nullptr;
     std::string err;
+    // tiled TMA maps of phi and of both velocity buffers for the step kernel's
+    // halo copies (FP32 arithmetic, rows of a multiple of 16 bytes)
+    bool tma = false;
+    CUtensorMap tm_phi{}, tm_u[2]{};
 
     template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
     void* N(int k) const { return at<void>(lay.off_N[k]); }
@@ -270,6 +275,7 @@ void launch_one_step(lbm_domain* d, int cur, cudaStream_t s, cudaEvent_t* ev = n
     sp.Nin = d->N(cur); sp.Bin = d->B(cur); sp.Nout = d->N(1 - cur); sp.Bout = d->B(1 - cur);
     sp.phi = d->phi(); sp.u_in = d->U(cur); sp.u_out = d->U(1 - cur); sp.p = d->p();
     sp.mask = d->mask(); sp.err = d->errflag();
+    if (d->tma) { sp.tm_phi = &d->tm_phi; sp.tm_u = &d->tm_u[cur]; }
     if (ev) cudaEventRecord(ev[1], s);
     dispatch(d, [&](auto Lx) { decltype(Lx)::step(d->cfg, sp, s); });
     if (ev) cudaEventRecord(ev[2], s);
@@ -290,10 +296,53 @@ lbm_status capture(lbm_domain* d, int start, int nsteps, cudaGraphExec_t* out) {
     return LBM_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link to libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        cudaGetLastError();
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor maps for the halo copies of the step kernel: phi as (nx, ny, nz) and
+// each velocity buffer as (nx, ny, nz, D) floats, box = the halo tile of
+// Tile<Q>.  Only for float fields whose rows are a multiple of 16 bytes (the
+// strides TMA accepts); otherwise, or if the driver refuses, the kernel copies
+// every halo element itself.
+template <int Q>
+bool make_halo_maps(lbm_domain* d) {
+    using Tl = Tile<Q>;
+    const lbm_params& P = d->prm;
+    if (d->fp64 || (P.nx * 4) % 16 != 0) return false;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const int D = Tl::D;
+    const cuuint64_t dims[4] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz, (cuuint64_t)D};
+    const cuuint64_t strides[3] = {(cuuint64_t)P.nx * 4, (cuuint64_t)P.nx * P.ny * 4, (cuuint64_t)d->lay.plane * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)Tl::HX, (cuuint32_t)Tl::HY, (cuuint32_t)Tl::HZ, (cuuint32_t)D};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    auto one = [&](CUtensorMap* m, void* base, cuuint32_t rank) {
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    return one(&d->tm_phi, d->phi(), 3) && one(&d->tm_u[0], d->U(0), 4) && one(&d->tm_u[1], d->U(1), 4);
+}
+
 lbm_status check_err_flag(lbm_domain* d) {
     int h = 0;
     CUDA_TRY(d, cudaMemcpyAsync(&h, d->errflag(), sizeof(int), cudaMemcpyDeviceToHost, d->stream));
     CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    if (h & kErrCopyTimeout) return fail(d, LBM_ERR_TIMEOUT, "a halo copy of the step kernel did not complete");
     if (h) return fail(d, LBM_ERR_UNSTABLE, "a step produced a non-finite velocity");
     return LBM_OK;
 }
@@ -492,6 +541,7 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
         return fail(nullptr, LBM_ERR_CUDA, msg);
     };
     if (cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking) != cudaSuccess) return bail("cudaStreamCreate failed");
+    d->tma = P.lattice == 9 ? make_halo_maps<9>(d) : make_halo_maps<19>(d);
     // upload node classes and the ghost table; the bounce-back mask is built on the device
     std::vector<int32_t> gnode(n_ghosts);
     for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)ghosts[g].node;

@@ -26,6 +26,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -162,7 +163,10 @@ struct Tile {
     static constexpr int TX = tile_extent(Q, V, 0);
     static constexpr int TY = tile_extent(Q, V, 1);
     static constexpr int TZ = tile_extent(Q, V, 2);
-    static constexpr int HX = TX + 2;
+    // halo tile: x from x0 - XO (a multiple of 4 for tiled TMA copies) to
+    // x0 + TX + XO - 1, y and z one node beyond the tile on each side
+    static constexpr int XO = 4;
+    static constexpr int HX = TX + 2 * XO;
     static constexpr int HY = TY + 2;
     static constexpr int HZ = (D == 2) ? 1 : TZ + 2;
     static constexpr int HN = HX * HY * HZ;
@@ -215,6 +219,51 @@ __device__ __forceinline__ void cp_async_value(T* dst_shared, const T* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ---- tiled TMA copies of the halo tile (cp.async.bulk.tensor), completed on
+// a shared-memory mbarrier.  A tile uses them only when its whole halo lies
+// inside the grid (no periodic image needed) and the grid's rows are a
+// multiple of 16 bytes; the copy origin x0 - 4 is then a multiple of 4 floats.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_addr(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_addr(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+// Waits for phase `parity` of the barrier; false if it has not completed after
+// kMbarSpins polls (the caller then flags an error instead of waiting on).
+constexpr int kMbarSpins = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (int k = 0; k < kMbarSpins; ++k) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// error flag bits: 1 = non-finite value, 2 = a halo copy did not complete
+constexpr int kErrNonFinite = 1, kErrCopyTimeout = 2;
+
 // Issues the copies of the halo tile; the caller waits (cp_async_wait_all,
 // then a barrier) before reading it.
 template <int Q, int V, typename T, bool LOAD_U>
@@ -234,8 +283,8 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __res
         const int gy = wrap_halo(y0 + hy - 1, P.ny);
         const int gz = (D == 2) ? 0 : wrap_halo(z0 + hz - 1, P.nz);
         const int rowbase = P.nx * (gy + P.ny * gz);
-        const int sbase = Tl::HX * r;
-        for (int e = lane; e < Tl::HX; e += 32) {
+        const int sbase = Tl::HX * r + Tl::XO - 1;                 // slot of x0 - 1
+        for (int e = lane; e < Tl::TX + 2; e += 32) {
             const int node = rowbase + wrap_halo(x0 + e - 1, P.nx);
             cp_async_value(s_phi + sbase + e, phi + node);
             if (LOAD_U) {
@@ -486,7 +535,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     using L = Lattice<Q>;
     using Tl = Tile<Q, V>;
     constexpr int D = L::D;
-    const int hc = (threadIdx.x + 1) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (D == 2 ? 0 : threadIdx.z + 1));
+    const int hc = (threadIdx.x + Tl::XO) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (D == 2 ? 0 : threadIdx.z + 1));
     const int pl = (int)P.plane;
     using PS = PopStore<S>;
     constexpr bool kShift = PS::kShift;
@@ -556,7 +605,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
 #pragma unroll
         for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
         b.p[node] = p;
-        if (!(u[0] * u[0] + u[1] * u[1] + u[2] * u[2] < 1e30)) atomicOr(b.err, 1);
+        if (!(u[0] * u[0] + u[1] * u[1] + u[2] * u[2] < 1e30)) atomicOr(b.err, kErrNonFinite);
         return;
     } else {
 #pragma unroll
@@ -726,7 +775,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
 #pragma unroll
     for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
     b.p[node] = p;
-    if (!(uu < T(1e30))) atomicOr(b.err, 1);   // also catches NaN
+    if (!(uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
     }
 }
 
@@ -735,8 +784,23 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
 // barrier each fluid node is updated.
 template <int Q, int V, typename T, typename S, bool CONTRAST>
 __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuffers<T, S>& b, T* s_phi, T* s_u,
-                                          int x0, int y0, int z0) {
-    load_halo<Q, V, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
+                                          int x0, int y0, int z0, const CUtensorMap* tm_phi = nullptr,
+                                          const CUtensorMap* tm_u = nullptr, uint64_t* bar = nullptr) {
+    using Tl = Tile<Q, V>;
+    // the halo by two tiled TMA copies when maps are given (interior tiles),
+    // else element by element with cp.async
+    const bool tma = tm_phi != nullptr;
+    if (tma) {
+        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) {
+            constexpr unsigned kBytes = (CONTRAST ? 1 + Tl::D : 1) * Tl::HN * sizeof(T);
+            mbar_expect_tx(bar, kBytes);
+            const int zc = Tl::D == 2 ? 0 : z0 - 1;
+            tma_load_3d(s_phi, tm_phi, x0 - Tl::XO, y0 - 1, zc, bar);
+            if (CONTRAST) tma_load_4d(s_u, tm_u, x0 - Tl::XO, y0 - 1, zc, 0, bar);
+        }
+    } else {
+        load_halo<Q, V, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
+    }
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     const bool in_grid = x < P.nx && y < P.ny && z < P.nz;
     const int node = in_grid ? x + P.nx * (y + P.ny * z) : 0;
@@ -745,9 +809,15 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
     if (in_grid) pull_streaming<Q, T, S>(P, b.Nin, node, x, y, z, N);      // in flight with the mask load
     const bool fluid = !(m & MASK_NOT_FLUID);
     if (fluid && (m & ~MASK_NOT_FLUID)) pull_bounce_back<Q, T, S>(P, b.Nin, m, node, N);
-    cp_async_wait_all();
+    bool halo_ok = true;
+    if (tma) {
+        halo_ok = mbar_wait(bar, 0);
+        if (!halo_ok && threadIdx.x + threadIdx.y + threadIdx.z == 0) atomicOr(b.err, kErrCopyTimeout);
+    } else {
+        cp_async_wait_all();
+    }
     __syncthreads();
-    if (fluid) step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, N, node);
+    if (fluid && halo_ok) step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, N, node);
 }
 
 // Resident blocks per SM the step kernels are compiled for (registers per
@@ -763,13 +833,27 @@ constexpr int step_min_blocks() {
     return StepOccupancy<T, S>::kBlocks * 256 / THREADS > 0 ? StepOccupancy<T, S>::kBlocks * 256 / THREADS : 1;
 }
 
+// tma != 0: the host made tensor maps of phi (nx, ny, nz) and of the previous
+// velocity (nx, ny, nz, D) with box (HX, HY, HZ[, D]); tiles whose halo lies
+// inside the grid copy it with them.
 template <int Q, typename T, typename S, bool CONTRAST, int V = 0>
 __global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Tile<Q, V>::THREADS>()))
-    k_step(StepParams<T> P, StepBuffers<T, S> b) {
+    k_step(StepParams<T> P, StepBuffers<T, S> b, const __grid_constant__ CUtensorMap tm_phi,
+           const __grid_constant__ CUtensorMap tm_u, int tma) {
     using Tl = Tile<Q, V>;
-    __shared__ T s_phi[Tl::HN];
-    __shared__ T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
-    step_tile<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, blockIdx.x * Tl::TX, blockIdx.y * Tl::TY, blockIdx.z * Tl::TZ);
+    __shared__ __align__(128) T s_phi[Tl::HN];
+    __shared__ __align__(128) T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
+    __shared__ __align__(8) uint64_t s_bar;
+    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
+    const bool interior = tma && x0 >= Tl::XO && x0 + Tl::TX + Tl::XO <= P.nx && y0 >= 1 && y0 + Tl::TY + 1 <= P.ny &&
+                          (Tl::D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= P.nz));
+    if (interior) {
+        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
+        __syncthreads();                                      // the barrier exists before anyone waits on it
+        step_tile<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, &tm_phi, &tm_u, &s_bar);
+    } else {
+        step_tile<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -40,6 +40,8 @@ struct StepPtrs {
     void* p;
     const uint32_t* mask;
     int* err;
+    const CUtensorMap* tm_phi = nullptr;   // tiled maps of phi and of u_in for the halo copies, or none
+    const CUtensorMap* tm_u = nullptr;
 };
 
 template <typename T, typename S>

@@ -47,10 +47,17 @@ void Launch<T, S>::step_q(const StepConfig& c, const StepPtrs& p, cudaStream_t s
     b.Nin = (const S*)p.Nin; b.Bin = (const S*)p.Bin; b.Nout = (S*)p.Nout; b.Bout = (S*)p.Bout;
     b.phi = (T*)p.phi; b.u_in = (const T*)p.u_in; b.u_out = (T*)p.u_out; b.p = (T*)p.p;
     b.mask = p.mask; b.err = p.err;
+    CUtensorMap tm_phi{}, tm_u{};
+    int tma = 0;
+    if (sizeof(T) == 4 && p.tm_phi && p.tm_u) {
+        tm_phi = *p.tm_phi;
+        tm_u = *p.tm_u;
+        tma = 1;
+    }
     if (c.contrast)
-        k_step<Q, T, S, true><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
+        k_step<Q, T, S, true><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b, tm_phi, tm_u, tma);
     else
-        k_step<Q, T, S, false><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b);
+        k_step<Q, T, S, false><<<step_grid<Q>(c.d), step_block<Q>(), 0, s>>>(P, b, tm_phi, tm_u, tma);
 }
 
 template <typename T, typename S>
