@@ -790,13 +790,31 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
     // the halo by two tiled TMA copies when maps are given (interior tiles),
     // else element by element with cp.async
     const bool tma = tm_phi != nullptr;
+    // At the x ends of the grid the box reads zeros where x < 0 or x >= nx; the
+    // stencil needs the periodic images of x = -1 and x = nx there: one thread
+    // per halo row and field loads such a value now and writes it once the
+    // copy has landed (fix_at >= 0).
+    T fix_v = T(0);
+    int fix_at = -1;
     if (tma) {
-        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) {
+        const int tid = threadIdx.x + Tl::TX * (threadIdx.y + Tl::TY * threadIdx.z);
+        if (tid == 0) {
             constexpr unsigned kBytes = (CONTRAST ? 1 + Tl::D : 1) * Tl::HN * sizeof(T);
             mbar_expect_tx(bar, kBytes);
             const int zc = Tl::D == 2 ? 0 : z0 - 1;
             tma_load_3d(s_phi, tm_phi, x0 - Tl::XO, y0 - 1, zc, bar);
             if (CONTRAST) tma_load_4d(s_u, tm_u, x0 - Tl::XO, y0 - 1, zc, 0, bar);
+        }
+        const bool lo = x0 == 0, hi = x0 + Tl::TX >= P.nx;
+        constexpr int kRows = Tl::HY * Tl::HZ, kPerCol = kRows * (CONTRAST ? 1 + Tl::D : 1);
+        if ((lo || hi) && tid < (int(lo) + int(hi)) * kPerCol) {
+            const bool left = lo && tid < kPerCol;              // x = -1, else x = nx
+            const int k = tid % kPerCol, field = k / kRows, r = k % kRows;
+            const int hy = r % Tl::HY, hz = r / Tl::HY;
+            const int gz = Tl::D == 2 ? 0 : z0 - 1 + hz;
+            const int node = (left ? P.nx - 1 : 0) + P.nx * (y0 - 1 + hy + P.ny * gz);
+            fix_v = field == 0 ? b.phi[node] : b.u_in[(field - 1) * (int)P.plane + node];
+            fix_at = (field == 0 ? 0 : Tl::HN * field) + (left ? Tl::XO - 1 : P.nx - x0 + Tl::XO) + Tl::HX * r;
         }
     } else {
         load_halo<Q, V, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
@@ -813,6 +831,7 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
     if (tma) {
         halo_ok = mbar_wait(bar, 0);
         if (!halo_ok && threadIdx.x + threadIdx.y + threadIdx.z == 0) atomicOr(b.err, kErrCopyTimeout);
+        if (fix_at >= 0) (fix_at < Tl::HN ? s_phi : s_u - Tl::HN)[fix_at] = fix_v;
     } else {
         cp_async_wait_all();
     }
@@ -845,7 +864,8 @@ __global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Ti
     __shared__ __align__(128) T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
     __shared__ __align__(8) uint64_t s_bar;
     const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
-    const bool interior = tma && x0 >= Tl::XO && x0 + Tl::TX + Tl::XO <= P.nx && y0 >= 1 && y0 + Tl::TY + 1 <= P.ny &&
+    // tiles whose halo needs no periodic image in y and z (x images are patched in step_tile)
+    const bool interior = tma && y0 >= 1 && y0 + Tl::TY + 1 <= P.ny &&
                           (Tl::D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= P.nz));
     if (interior) {
         if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
