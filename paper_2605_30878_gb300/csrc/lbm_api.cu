@@ -841,6 +841,7 @@ struct lbm_batch {
     std::vector<int> slots;            // each domain's slot of the constant table
     char* dev = nullptr;               // one allocation for every device table
     int4* tiles[kTileVariants] = {};             // {slot, x0, y0, z0}
+    CUtensorMap* maps = nullptr;                 // [kBatchSlots][3] halo maps by slot (see k_step_batched)
     void* ghost_tabs = nullptr;
     int64_t* ghost_begin = nullptr;
     int64_t total_ghosts = 0;
@@ -906,7 +907,7 @@ void batch_launch_step(lbm_batch* b, int parity, cudaStream_t s) {
     bdispatch(b->precision, [&](auto Lx) {
         using L = decltype(Lx);
         L::ghost_batched(b->GK, b->ghost_tabs, b->ghost_begin, (int)b->doms.size(), b->total_ghosts, s);
-        L::step_phi_batched(b->Q, V, b->tiles[V], b->ntiles[V], b->ncontrast[V], parity, s);
+        L::step_phi_batched(b->Q, V, b->tiles[V], b->maps, b->ntiles[V], b->ncontrast[V], parity, s);
     });
 }
 
@@ -991,7 +992,7 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
                 sp[k].phi = d->phi(); sp[k].u_in = d->U(c); sp[k].u_out = d->U(1 - c); sp[k].p = d->p();
                 sp[k].mask = d->mask(); sp[k].err = d->errflag();
             }
-            LL::fill_entry(&he[esz * i], d->cfg, sp);
+            LL::fill_entry(&he[esz * i], d->cfg, sp, d->tma);
             LL::fill_ghost_table(&hg[gsz * i], d->ng, d->at<int32_t>(L.off_gnode), d->at<int32_t>(L.off_gcorner),
                                  d->at<void>(L.off_gwt), d->cfg.exp_eps, d->cfg.eps, d->phi(), d->cfg.ghost_rule);
         });
@@ -1010,6 +1011,17 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t r = off; off = round_up(off + bytes, 256); return r; };
     const size_t o_g = take(hg.size()), o_gb = take(gbegin.size() * 8);
+    // halo maps by slot: phi, then u_in of step parity 0 and 1 (u_in = U(cur0 ^ parity))
+    std::vector<CUtensorMap> hm((size_t)kBatchSlots * 3);
+    for (int i = 0; i < n; ++i) {
+        lbm_domain* d = b->doms[i];
+        if (!d->tma) continue;
+        const int sl = b->slots[i];
+        hm[3 * sl] = d->tm_phi;
+        hm[3 * sl + 1] = d->tm_u[b->cur0[i]];
+        hm[3 * sl + 2] = d->tm_u[b->cur0[i] ^ 1];
+    }
+    const size_t o_m = take(hm.size() * sizeof(CUtensorMap));
     size_t o_t[kTileVariants];
     for (int V = 0; V < kTileVariants; ++V) {
         if (tiles[V].size() > (size_t)INT32_MAX) {
@@ -1025,7 +1037,8 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
     }
     b->ghost_tabs = b->dev + o_g;
     b->ghost_begin = (int64_t*)(b->dev + o_gb);
-    cudaError_t e = cudaSuccess;
+    b->maps = (CUtensorMap*)(b->dev + o_m);
+    cudaError_t e = cudaMemcpy(b->maps, hm.data(), hm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
     for (int i = 0; i < n && e == cudaSuccess; ++i)
         bdispatch(b->precision, [&](auto Lx) { e = decltype(Lx)::upload_entries(b->slots[i], &he[esz * i], 1); });
     if (e == cudaSuccess) e = cudaMemcpy(b->ghost_tabs, hg.data(), hg.size(), cudaMemcpyHostToDevice);

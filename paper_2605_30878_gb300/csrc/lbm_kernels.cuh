@@ -893,20 +893,35 @@ template <typename T, typename S>
 struct BatchEntry {
     StepParams<T> P;
     StepBuffers<T, S> b[2];
+    int tma;                           // the batch's map table holds this slot's halo maps
 };
 
 template <typename T, typename S>
 __constant__ BatchEntry<T, S> c_batch[kBatchSlots];
 
+// maps: tiled TMA maps of the halo fields, three per slot (phi, then u_in for
+// step parity 0 and 1), in global memory; used with tile shape 0 (the shape
+// the maps' boxes are made for) on tiles needing no periodic image in y, z.
 template <int Q, typename T, typename S, int V, bool CONTRAST>
 __global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Tile<Q, V>::THREADS>()))
-    k_step_batched(const int4* __restrict__ tiles, int parity) {
+    k_step_batched(const int4* __restrict__ tiles, const CUtensorMap* __restrict__ maps, int parity) {
     using Tl = Tile<Q, V>;
-    __shared__ T s_phi[Tl::HN];
-    __shared__ T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
+    __shared__ __align__(128) T s_phi[Tl::HN];
+    __shared__ __align__(128) T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
+    __shared__ __align__(8) uint64_t s_bar;
     const int4 t = __ldg(tiles + blockIdx.x);          // {slot, x0, y0, z0}
     const BatchEntry<T, S>& e = c_batch<T, S>[t.x];
-    step_tile<Q, V, T, S, CONTRAST>(e.P, e.b[parity], s_phi, s_u, t.y, t.z, t.w);
+    const int y0 = t.z, z0 = t.w;
+    const bool tma = V == 0 && maps != nullptr && e.tma && y0 >= 1 && y0 + Tl::TY + 1 <= e.P.ny &&
+                     (Tl::D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= e.P.nz));
+    if (tma) {
+        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
+        __syncthreads();                                      // the barrier exists before anyone waits on it
+        step_tile<Q, V, T, S, CONTRAST>(e.P, e.b[parity], s_phi, s_u, t.y, y0, z0, maps + 3 * t.x,
+                                        maps + 3 * t.x + 1 + parity, &s_bar);
+    } else {
+        step_tile<Q, V, T, S, CONTRAST>(e.P, e.b[parity], s_phi, s_u, t.y, y0, z0);
+    }
 }
 
 template <int Q, typename T, typename S, int V>

@@ -70,15 +70,16 @@ struct Launch {
                            cudaStream_t s);
     // ---- batched launches (one block per tile of a flat tile list)
     template <int Qc, int V>
-    static void step_batched_v(const int4* tiles, int ntiles, int ncontrast, int parity, cudaStream_t s);
+    static void step_batched_v(const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast, int parity,
+                               cudaStream_t s);
     // step kernels then color kernel of every domain (the ghost update precedes them);
     // tiles[0, ncontrast) belong to domains with density contrast
-    static void step_phi_batched(int Q, int V, const int4* tiles, int ntiles, int ncontrast, int parity,
-                                 cudaStream_t s);
+    static void step_phi_batched(int Q, int V, const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast,
+                                 int parity, cudaStream_t s);
     // Slot tables: entry_size() bytes per domain, filled by fill_entry, copied
     // to slots [slot0, slot0 + n) of the constant table by upload_entries.
     static size_t entry_size() { return sizeof(BatchEntry<T, S>); }
-    static void fill_entry(void* out, const StepConfig& c, const StepPtrs p[2]);
+    static void fill_entry(void* out, const StepConfig& c, const StepPtrs p[2], bool tma);
     static cudaError_t upload_entries(int slot0, const void* entries, int n);
     static void ghost_batched(int GK, const void* tabs, const int64_t* begin, int ndom, int64_t total, cudaStream_t s);
     static size_t ghost_table_size() { return sizeof(GhostTable<T>); }

@@ -155,39 +155,41 @@ void Launch<T, S>::gather_dir(const StepConfig& c, const uint8_t* cls, int i, bo
 // ---- batched launches (one block per tile of a flat tile list)
 template <typename T, typename S>
 template <int Qc, int V>
-void Launch<T, S>::step_batched_v(const int4* tiles, int ntiles, int ncontrast, int parity, cudaStream_t s) {
+void Launch<T, S>::step_batched_v(const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast, int parity,
+                                  cudaStream_t s) {
     using Tl = Tile<Qc, V>;
     const dim3 block(Tl::TX, Tl::TY, Tl::TZ);     // the tile shape, as in the single-domain kernels
     if (ncontrast > 0)
-        k_step_batched<Qc, T, S, V, true><<<ncontrast, block, 0, s>>>(tiles, parity);
+        k_step_batched<Qc, T, S, V, true><<<ncontrast, block, 0, s>>>(tiles, maps, parity);
     if (ntiles > ncontrast)
-        k_step_batched<Qc, T, S, V, false><<<ntiles - ncontrast, block, 0, s>>>(tiles + ncontrast, parity);
+        k_step_batched<Qc, T, S, V, false><<<ntiles - ncontrast, block, 0, s>>>(tiles + ncontrast, maps, parity);
     k_phi_batched<Qc, T, S, V><<<ntiles, block, 0, s>>>(tiles, parity);
 }
 
 // step kernels then color kernel of every domain (the ghost update precedes them);
 // tiles[0, ncontrast) belong to domains with density contrast
 template <typename T, typename S>
-void Launch<T, S>::step_phi_batched(int Q, int V, const int4* tiles, int ntiles, int ncontrast, int parity,
+void Launch<T, S>::step_phi_batched(int Q, int V, const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast,
+                                      int parity,
                              cudaStream_t s) {
     if (ntiles == 0) return;
     if (Q == 9) {
-        if (V == 0) step_batched_v<9, 0>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 1) step_batched_v<9, 1>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 2) step_batched_v<9, 2>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 3) step_batched_v<9, 3>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 4) step_batched_v<9, 4>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 0) step_batched_v<9, 0>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 1) step_batched_v<9, 1>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 2) step_batched_v<9, 2>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 3) step_batched_v<9, 3>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 4) step_batched_v<9, 4>(tiles, maps, ntiles, ncontrast, parity, s);
     } else {
-        if (V == 0) step_batched_v<19, 0>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 1) step_batched_v<19, 1>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 2) step_batched_v<19, 2>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 3) step_batched_v<19, 3>(tiles, ntiles, ncontrast, parity, s);
-        if (V == 4) step_batched_v<19, 4>(tiles, ntiles, ncontrast, parity, s);
+        if (V == 0) step_batched_v<19, 0>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 1) step_batched_v<19, 1>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 2) step_batched_v<19, 2>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 3) step_batched_v<19, 3>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 4) step_batched_v<19, 4>(tiles, maps, ntiles, ncontrast, parity, s);
     }
 }
 
 template <typename T, typename S>
-void Launch<T, S>::fill_entry(void* out, const StepConfig& c, const StepPtrs p[2]) {
+void Launch<T, S>::fill_entry(void* out, const StepConfig& c, const StepPtrs p[2], bool tma) {
     BatchEntry<T, S> e;
     e.P = params(c);
     for (int k = 0; k < 2; ++k) {
@@ -196,6 +198,7 @@ void Launch<T, S>::fill_entry(void* out, const StepConfig& c, const StepPtrs p[2
         b.phi = (T*)p[k].phi; b.u_in = (const T*)p[k].u_in; b.u_out = (T*)p[k].u_out; b.p = (T*)p[k].p;
         b.mask = p[k].mask; b.err = p[k].err;
     }
+    e.tma = (sizeof(T) == 4 && tma) ? 1 : 0;
     std::memcpy(out, &e, sizeof(e));
 }
 

@@ -176,18 +176,24 @@ def test_batch_size_limit():
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16])
 @pytest.mark.parametrize("Q", [9, 19])
 def test_tma_halo_equals_element_copies(precision, Q):
-    """Large enough for interior tiles: the single-domain step kernel copies
-    their halo with tiled TMA loads, the batched kernel element by element;
-    the states must agree to the bit."""
+    """Large enough for tiles whose halo needs no periodic image in y, z: the
+    single-domain step kernel copies their halo with tiled TMA loads from
+    kernel-parameter maps, the batched kernel with tile shape 0 from maps in
+    global memory, and with tile shape 1 element by element; the three states
+    must agree to the bit."""
     if Q == 19:
         cfg = wl.sphere_config(n=96, R=20.0, R0=14.0, theta_deg=70.0, rho_ratio=1000.0, precision=precision)
     else:
         cfg = wl.cylinder_config(nx=160, ny=128, R=20.0, R0=16.0, theta_deg=110.0)
         cfg["params"].update(precision=precision, rho_l=1000.0, rho_g=1.0, mu_l=10.0, mu_g=0.1)
-    alone, mixed = _make([cfg]), _make([cfg])
+    alone, mixed, copied = _make([cfg]), _make([cfg]), _make([cfg])
     alone[0].step(9)
-    with lbm.Batch(mixed) as b:
-        b.step(9)
-        b.sync()
+    for doms, variant in ((mixed, 0), (copied, 1)):
+        with lbm.Batch(doms) as b:
+            b.set_variant(variant)
+            b.step(9)
+            b.sync()
     for f in ("N", "B", "phi", "u", "p"):
-        assert np.array_equal(alone[0].read(f), mixed[0].read(f)), f
+        a = alone[0].read(f)
+        assert np.array_equal(a, mixed[0].read(f)), ("TMA, global maps", f)
+        assert np.array_equal(a, copied[0].read(f)), ("element copies", f)
