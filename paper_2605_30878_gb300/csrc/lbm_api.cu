@@ -29,7 +29,9 @@ constexpr int GRAPH_STEPS = 8;
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-    int64_t nn = 0, plane = 0;
+    int px = 0;                      // row pitch of the device fields: nx rounded up to 4 (16-byte rows)
+    int64_t nn = 0, plane = 0;       // device nodes px * ny * nz (columns nx..px-1 are solid padding)
+    int64_t nn_dense = 0;            // grid nodes nx * ny * nz (host arrays)
     size_t elem = 0;                 // bytes of a field value (phi, u, p, ghost weights)
     size_t pop_elem = 0;             // bytes of a stored moving population
     size_t rest_elem = 0;            // bytes of a stored rest population
@@ -50,7 +52,9 @@ bool make_layout(const lbm_params* P, int64_t ng, Layout& L, std::string& err) {
     if (P->nx < 1 || P->ny < 1 || P->nz < 1) { err = "grid sizes must be positive"; return false; }
     if (P->lattice == LBM_D2Q9 && P->nz != 1) { err = "D2Q9 needs nz == 1"; return false; }
     if (ng < 0) { err = "n_ghosts must be >= 0"; return false; }
-    const int64_t nn = (int64_t)P->nx * P->ny * P->nz;
+    L.px = (int)round_up((size_t)P->nx, 4);
+    L.nn_dense = (int64_t)P->nx * P->ny * P->nz;
+    const int64_t nn = (int64_t)L.px * P->ny * P->nz;
     if (nn >= ((int64_t)1 << 31)) { err = "grid has 2^31 nodes or more"; return false; }
     L.nn = nn;
     L.plane = (int64_t)round_up((size_t)nn, 64);
@@ -123,6 +127,14 @@ struct lbm_domain {
 };
 
 namespace {
+// device index of grid node x + nx * (y + ny * z): x + px * (y + ny * z)
+int64_t padded_node(const lbm_domain* d, int64_t node) {
+    const int64_t nx = d->prm.nx;
+    return node % nx + (int64_t)d->lay.px * (node / nx);
+}
+}  // namespace
+
+namespace {
 
 lbm_status fail(lbm_domain* d, lbm_status s, const std::string& msg) {
     if (d) d->err = msg; else g_create_error = msg;
@@ -186,10 +198,10 @@ lbm_status prepare_ghosts(lbm_domain* d, const lbm_ghost* ghosts) {
     d->h_nc.assign(ng, 0);
     std::vector<int> ox, oy, oz;
     stencil_offsets(P.lattice, ox, oy, oz);
-    std::vector<uint8_t> seen(d->lay.nn, 0);
+    std::vector<uint8_t> seen(d->lay.nn_dense, 0);
     for (int64_t g = 0; g < ng; ++g) {
         const int64_t node = ghosts[g].node;
-        if (node < 0 || node >= d->lay.nn || d->h_cls[node] != CLS_GHOST)
+        if (node < 0 || node >= d->lay.nn_dense || d->h_cls[node] != CLS_GHOST)
             return fail(nullptr, LBM_ERR_ARG, "ghost " + std::to_string(g) + " (node " + std::to_string(node) +
                                                   ") is not a solid node with a fluid neighbour");
         if (seen[node]) return fail(nullptr, LBM_ERR_ARG, "node " + std::to_string(node) + " is listed twice");
@@ -322,12 +334,13 @@ template <int Q>
 bool make_halo_maps(lbm_domain* d) {
     using Tl = Tile<Q>;
     const lbm_params& P = d->prm;
-    if (d->fp64 || (P.nx * 4) % 16 != 0) return false;
+    if (d->fp64) return false;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
     const int D = Tl::D;
     const cuuint64_t dims[4] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz, (cuuint64_t)D};
-    const cuuint64_t strides[3] = {(cuuint64_t)P.nx * 4, (cuuint64_t)P.nx * P.ny * 4, (cuuint64_t)d->lay.plane * 4};
+    const cuuint64_t strides[3] = {(cuuint64_t)d->lay.px * 4, (cuuint64_t)d->lay.px * P.ny * 4,
+                                   (cuuint64_t)d->lay.plane * 4};
     const cuuint32_t box[4] = {(cuuint32_t)Tl::HX, (cuuint32_t)Tl::HY, (cuuint32_t)Tl::HZ, (cuuint32_t)D};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
     auto one = [&](CUtensorMap* m, void* base, cuuint32_t rank) {
@@ -348,30 +361,41 @@ lbm_status check_err_flag(lbm_domain* d) {
 }
 
 // host double <-> device T conversions through a staging vector
-lbm_status upload(lbm_domain* d, void* dst, const double* src, size_t count) {
-    if (d->fp64) {
-        CUDA_TRY(d, cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyHostToDevice, d->stream));
-        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
-    } else {
-        std::vector<float> tmp(count);
-        for (size_t k = 0; k < count; ++k) tmp[k] = (float)src[k];
-        CUDA_TRY(d, cudaMemcpyAsync(dst, tmp.data(), count * 4, cudaMemcpyHostToDevice, d->stream));
-        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
-    }
+// One whole field between a dense host array of doubles (nx * ny * nz values)
+// and the device (field type, rows padded to px; the padding holds zeros).
+template <typename V>
+lbm_status upload_as(lbm_domain* d, void* dst, const double* src) {
+    const Layout& L = d->lay;
+    const int64_t nx = d->prm.nx, rows = L.nn_dense / nx;
+    std::vector<V> tmp((size_t)L.nn, V(0));
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t x = 0; x < nx; ++x) tmp[(size_t)(r * L.px + x)] = (V)src[r * nx + x];
+    CUDA_TRY(d, cudaMemcpyAsync(dst, tmp.data(), tmp.size() * sizeof(V), cudaMemcpyHostToDevice, d->stream));
+    CUDA_TRY(d, cudaStreamSynchronize(d->stream));
     return LBM_OK;
 }
 
-lbm_status download(lbm_domain* d, double* dst, const void* src, size_t count) {
-    if (d->fp64) {
-        CUDA_TRY(d, cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyDeviceToHost, d->stream));
-        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
-    } else {
-        std::vector<float> tmp(count);
-        CUDA_TRY(d, cudaMemcpyAsync(tmp.data(), src, count * 4, cudaMemcpyDeviceToHost, d->stream));
-        CUDA_TRY(d, cudaStreamSynchronize(d->stream));
-        for (size_t k = 0; k < count; ++k) dst[k] = (double)tmp[k];
-    }
+template <typename V>
+lbm_status download_as(lbm_domain* d, double* dst, const void* src) {
+    const Layout& L = d->lay;
+    const int64_t nx = d->prm.nx, rows = L.nn_dense / nx;
+    std::vector<V> tmp((size_t)L.nn);
+    CUDA_TRY(d, cudaMemcpyAsync(tmp.data(), src, tmp.size() * sizeof(V), cudaMemcpyDeviceToHost, d->stream));
+    CUDA_TRY(d, cudaStreamSynchronize(d->stream));
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t x = 0; x < nx; ++x) dst[r * nx + x] = (double)tmp[(size_t)(r * L.px + x)];
     return LBM_OK;
+}
+
+// count must be the grid's node count: whole fields only
+lbm_status upload(lbm_domain* d, void* dst, const double* src, size_t count) {
+    if ((int64_t)count != d->lay.nn_dense) return fail(d, LBM_ERR_ARG, "field size mismatch");
+    return d->fp64 ? upload_as<double>(d, dst, src) : upload_as<float>(d, dst, src);
+}
+
+lbm_status download(lbm_domain* d, double* dst, const void* src, size_t count) {
+    if ((int64_t)count != d->lay.nn_dense) return fail(d, LBM_ERR_ARG, "field size mismatch");
+    return d->fp64 ? download_as<double>(d, dst, src) : download_as<float>(d, dst, src);
 }
 
 lbm_status init_state(lbm_domain* d, int mode, const double ctr[3], double R0) {
@@ -465,7 +489,7 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     if (!(alpha > 0.0 && alpha < 1.0)) { delete d; return fail(nullptr, LBM_ERR_ARG, "M_phi gives alpha outside (0,1)"); }
     c.Q = P.lattice;
     c.contrast = d->contrast;
-    c.d = Dims{P.nx, P.ny, P.nz, L.plane, P.periodic};
+    c.d = Dims{P.nx, P.ny, P.nz, L.px, L.plane, P.periodic};
     c.rho_l = P.rho_l; c.rho_g = P.rho_g;
     c.nu_l = P.mu_l / P.rho_l; c.nu_g = P.mu_g / P.rho_g;
     c.sigma = P.sigma; c.W = P.W;
@@ -476,7 +500,7 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     c.ghost_rule = P.ghost_rule;
 
     // node classes: a solid node with a fluid stencil neighbour is a ghost
-    const int64_t nn = L.nn;
+    const int64_t nn = L.nn_dense;
     const int64_t nx = P.nx, ny = P.ny, nz = P.nz;
     d->h_cls.assign(nn, CLS_FLUID);
     std::vector<int> ox, oy, oz;
@@ -543,17 +567,21 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     if (cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking) != cudaSuccess) return bail("cudaStreamCreate failed");
     d->tma = P.lattice == 9 ? make_halo_maps<9>(d) : make_halo_maps<19>(d);
     // upload node classes and the ghost table; the bounce-back mask is built on the device
-    std::vector<int32_t> gnode(n_ghosts);
-    for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)ghosts[g].node;
+    // device node indices use the padded row pitch
+    std::vector<int32_t> gnode(n_ghosts), pcorner(d->h_corner.size());
+    for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)padded_node(d, ghosts[g].node);
+    for (size_t k = 0; k < pcorner.size(); ++k) pcorner[k] = (int32_t)padded_node(d, d->h_corner[k]);
+    std::vector<uint8_t> pcls((size_t)L.nn, CLS_SOLID);
+    for (int64_t k = 0; k < nn; ++k) pcls[padded_node(d, k)] = d->h_cls[k];
     cudaStream_t s = d->stream;
     if (cudaMemsetAsync(d->ws, 0, L.total, s) != cudaSuccess) return bail("cudaMemset failed");
-    if (cudaMemcpyAsync(d->cls(), d->h_cls.data(), nn, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(d->cls(), pcls.data(), L.nn, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return bail("upload of node classes failed");
     dispatch(d, [&](auto Lx) { decltype(Lx)::build_mask(d->cfg, d->cls(), d->mask(), s); });
     if (cudaGetLastError() != cudaSuccess) return bail("launch of the mask kernel failed");
     if (n_ghosts > 0) {
         if (cudaMemcpyAsync(d->at<void>(L.off_gnode), gnode.data(), n_ghosts * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(d->at<void>(L.off_gcorner), d->h_corner.data(), d->h_corner.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            cudaMemcpyAsync(d->at<void>(L.off_gcorner), pcorner.data(), pcorner.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return bail("upload of the ghost table failed");
         if (d->fp64) {
             if (cudaMemcpyAsync(d->at<void>(L.off_gwt), d->h_wt.data(), d->h_wt.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -581,7 +609,7 @@ lbm_status lbm_init_droplet(lbm_domain* d, const double centre[3], double R0) {
 
 lbm_status lbm_init_phi(lbm_domain* d, const double* phi_host) {
     if (!d || !phi_host) return fail(d, LBM_ERR_ARG, "NULL argument");
-    lbm_status st = upload(d, d->phi(), phi_host, d->lay.nn);
+    lbm_status st = upload(d, d->phi(), phi_host, d->lay.nn_dense);
     if (st != LBM_OK) return st;
     const double zero[3] = {0, 0, 0};
     return init_state(d, 1, zero, 1.0);
@@ -708,7 +736,7 @@ lbm_status lbm_diagnostics(lbm_domain* d, const lbm_probe* probe, lbm_diag* out)
 lbm_status lbm_read_state(lbm_domain* d, int32_t field, double* host_out) {
     if (!d || !host_out) return fail(d, LBM_ERR_ARG, "NULL argument");
     const Layout& L = d->lay;
-    const int64_t nn = L.nn;
+    const int64_t nn = L.nn_dense;
     std::vector<double> tmp;
     switch (field) {
     case LBM_FIELD_N:
@@ -746,7 +774,7 @@ lbm_status lbm_read_state(lbm_domain* d, int32_t field, double* host_out) {
 lbm_status lbm_write_state(lbm_domain* d, int32_t field, const double* host_in) {
     if (!d || !host_in) return fail(d, LBM_ERR_ARG, "NULL argument");
     const Layout& L = d->lay;
-    const int64_t nn = L.nn;
+    const int64_t nn = L.nn_dense;
     switch (field) {
     case LBM_FIELD_N:
     case LBM_FIELD_B: {

@@ -8,21 +8,25 @@
 
 namespace lbmgpu {
 
+// Grid extents, the row pitch px >= nx of every device field (node = x + px *
+// (y + ny * z); columns nx..px-1 are solid padding) and the plane stride.
 struct Dims {
-    int nx, ny, nz;
+    int nx, ny, nz, px;
     int64_t plane;
     uint32_t periodic;
 };
 
+__device__ __forceinline__ int64_t padded_nodes(const Dims& d) { return (int64_t)d.px * d.ny * d.nz; }
+
 __device__ __forceinline__ void node_xyz(int64_t node, const Dims& d, int& x, int& y, int& z) {
-    x = (int)(node % d.nx);
-    y = (int)((node / d.nx) % d.ny);
-    z = (int)(node / ((int64_t)d.nx * d.ny));
+    x = (int)(node % d.px);
+    y = (int)((node / d.px) % d.ny);
+    z = (int)(node / ((int64_t)d.px * d.ny));
 }
 
 __device__ __forceinline__ int64_t shifted(const Dims& d, int x, int y, int z, int dx, int dy, int dz) {
     const int xx = wrap_any(x + dx, d.nx), yy = wrap_any(y + dy, d.ny), zz = wrap_any(z + dz, d.nz);
-    return xx + (int64_t)d.nx * (yy + (int64_t)d.ny * zz);
+    return xx + (int64_t)d.px * (yy + (int64_t)d.ny * zz);
 }
 
 // Per-node bounce-back mask from the node classes: bit i (1 <= i < Q) set when
@@ -30,7 +34,7 @@ __device__ __forceinline__ int64_t shifted(const Dims& d, int x, int y, int z, i
 template <int Q>
 __global__ void k_build_mask(Dims d, const uint8_t* __restrict__ cls, uint32_t* __restrict__ mask) {
     using L = Lattice<Q>;
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = padded_nodes(d);
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {
         if (cls[node] != CLS_FLUID) {
@@ -46,7 +50,7 @@ __global__ void k_build_mask(Dims d, const uint8_t* __restrict__ cls, uint32_t* 
             xx += xx < 0 ? d.nx : (xx >= d.nx ? -d.nx : 0);
             yy += yy < 0 ? d.ny : (yy >= d.ny ? -d.ny : 0);
             zz += zz < 0 ? d.nz : (zz >= d.nz ? -d.nz : 0);
-            if (cls[xx + (int64_t)d.nx * (yy + (int64_t)d.ny * zz)] != CLS_FLUID) m |= 1u << i;
+            if (cls[xx + (int64_t)d.px * (yy + (int64_t)d.ny * zz)] != CLS_FLUID) m |= 1u << i;
         }
         mask[node] = m;
     }
@@ -57,7 +61,7 @@ __global__ void k_build_mask(Dims d, const uint8_t* __restrict__ cls, uint32_t* 
 template <int D, typename T>
 __global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restrict__ phi, int mode, double cx,
                            double cy, double cz, double R0, double W, double ghost_value) {
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = padded_nodes(d);
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t c = cls[node];
@@ -91,7 +95,7 @@ __global__ void k_init_pops(Dims d, StepParams<T> P, const uint8_t* __restrict__
                             S* __restrict__ Nst, S* __restrict__ Bst) {
     using L = Lattice<Q>;
     constexpr bool kShift = PopStore<S>::kShift;
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = padded_nodes(d);
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {
         if (cls[node] != CLS_FLUID) continue;
@@ -114,7 +118,7 @@ template <int Q, typename T, typename S>
 __global__ void k_scatter_dir(Dims d, const uint8_t* __restrict__ cls, int i, const T* __restrict__ post_i,
                               const T* __restrict__ post_opp, T base, float scale, S* __restrict__ st) {
     using L = Lattice<Q>;
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = padded_nodes(d);
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {
         if (cls[node] != CLS_FLUID) continue;
@@ -131,7 +135,7 @@ template <int Q, typename T, typename S>
 __global__ void k_gather_dir(Dims d, const uint8_t* __restrict__ cls, int i, const S* __restrict__ st, T base,
                              float scale, T* __restrict__ post) {
     using L = Lattice<Q>;
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = padded_nodes(d);
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {
         T v = T(0);
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rh
 #pragma unroll
     for (int k = 0; k < DG_REC; ++k) acc[k] = 0.0;
     acc[DG_APEX] = -INFINITY;
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = padded_nodes(d);
     const int n[3] = {d.nx, d.ny, d.nz};
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
          node += (int64_t)gridDim.x * blockDim.x) {

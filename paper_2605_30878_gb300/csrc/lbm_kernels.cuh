@@ -39,6 +39,7 @@ enum : uint8_t { CLS_FLUID = 0, CLS_GHOST = 1, CLS_SOLID = 2 };
 template <typename T>
 struct StepParams {
     int nx, ny, nz;
+    int px;                  // row pitch: node = x + px * (y + ny * z), px = nx rounded up to 4
     int64_t plane;           // elements between consecutive planes of a field
     T rho_l, rho_g, drho;    // drho = rho_l - rho_g
     T inv_nu_l, inv_nu_g;    // 1/nu_l, 1/nu_g
@@ -188,15 +189,16 @@ __device__ __forceinline__ int wrap_halo(int v, int n) {
     return v < n ? v : 0;
 }
 
-// Linear offsets (32-bit) from node (x, y, z) to its periodic lattice neighbours.
+// Linear offsets (32-bit) from node (x, y, z) to its periodic lattice
+// neighbours, rows px apart.
 struct Wrap {
     int xm, xp, ym, yp, zm, zp;
-    __device__ __forceinline__ Wrap(int x, int y, int z, int nx, int ny, int nz) {
+    __device__ __forceinline__ Wrap(int x, int y, int z, int nx, int ny, int nz, int px) {
         xm = (x == 0) ? nx - 1 : -1;
         xp = (x == nx - 1) ? 1 - nx : 1;
-        ym = (y == 0) ? (ny - 1) * nx : -nx;
-        yp = (y == ny - 1) ? (1 - ny) * nx : nx;
-        const int sz = nx * ny;
+        ym = (y == 0) ? (ny - 1) * px : -px;
+        yp = (y == ny - 1) ? (1 - ny) * px : px;
+        const int sz = px * ny;
         zm = (z == 0) ? (nz - 1) * sz : -sz;
         zp = (z == nz - 1) ? (1 - nz) * sz : sz;
     }
@@ -282,7 +284,7 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __res
         const int hy = r % Tl::HY, hz = r / Tl::HY;
         const int gy = wrap_halo(y0 + hy - 1, P.ny);
         const int gz = (D == 2) ? 0 : wrap_halo(z0 + hz - 1, P.nz);
-        const int rowbase = P.nx * (gy + P.ny * gz);
+        const int rowbase = P.px * (gy + P.ny * gz);
         const int sbase = Tl::HX * r + Tl::XO - 1;                 // slot of x0 - 1
         for (int e = lane; e < Tl::TX + 2; e += 32) {
             const int node = rowbase + wrap_halo(x0 + e - 1, P.nx);
@@ -303,10 +305,10 @@ __device__ __forceinline__ void phi_node(const StepParams<T>& P, const S* __rest
                                          const uint32_t* __restrict__ mask, T* __restrict__ phi, int x, int y, int z) {
     using L = Lattice<Q>;
     if (x >= P.nx || y >= P.ny || z >= P.nz) return;
-    const int node = x + P.nx * (y + P.ny * z);
+    const int node = x + P.px * (y + P.ny * z);
     const uint32_t m = __ldg(mask + node);
     if (m & MASK_NOT_FLUID) return;
-    const Wrap W(x, y, z, P.nx, P.ny, P.nz);
+    const Wrap W(x, y, z, P.nx, P.ny, P.nz, P.px);
     const int pl = (int)P.plane;
     using PS = PopStore<S>;
     const auto* mv = PS::moving(Bst, pl);
@@ -487,7 +489,7 @@ __device__ __forceinline__ void pull_node(const StepParams<T>& P, const S* __res
                                           int x, int y, int z, T (&N)[Q]) {
     using L = Lattice<Q>;
     using PS = PopStore<S>;
-    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz);
+    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz, P.px);
     const int pl = (int)P.plane;
     N[0] = (T)PS::load_rest(PS::rest(Nin), node);
     const auto* mv = PS::moving(Nin, pl);
@@ -507,7 +509,7 @@ __device__ __forceinline__ void pull_streaming(const StepParams<T>& P, const S* 
                                                int y, int z, T (&N)[Q]) {
     using L = Lattice<Q>;
     using PS = PopStore<S>;
-    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz);
+    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz, P.px);
     const int pl = (int)P.plane;
     N[0] = (T)PS::load_rest(PS::rest(Nin), node);
     const auto* mv = PS::moving(Nin, pl);
@@ -812,7 +814,7 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
             const int k = tid % kPerCol, field = k / kRows, r = k % kRows;
             const int hy = r % Tl::HY, hz = r / Tl::HY;
             const int gz = Tl::D == 2 ? 0 : z0 - 1 + hz;
-            const int node = (left ? P.nx - 1 : 0) + P.nx * (y0 - 1 + hy + P.ny * gz);
+            const int node = (left ? P.nx - 1 : 0) + P.px * (y0 - 1 + hy + P.ny * gz);
             fix_v = field == 0 ? b.phi[node] : b.u_in[(field - 1) * (int)P.plane + node];
             fix_at = (field == 0 ? 0 : Tl::HN * field) + (left ? Tl::XO - 1 : P.nx - x0 + Tl::XO) + Tl::HX * r;
         }
@@ -821,7 +823,7 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
     }
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     const bool in_grid = x < P.nx && y < P.ny && z < P.nz;
-    const int node = in_grid ? x + P.nx * (y + P.ny * z) : 0;
+    const int node = in_grid ? x + P.px * (y + P.ny * z) : 0;
     const uint32_t m = in_grid ? __ldg(b.mask + node) : MASK_NOT_FLUID;
     T N[Q];
     if (in_grid) pull_streaming<Q, T, S>(P, b.Nin, node, x, y, z, N);      // in flight with the mask load

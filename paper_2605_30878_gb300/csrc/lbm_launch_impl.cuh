@@ -11,6 +11,7 @@ template <typename T, typename S>
 StepParams<T> Launch<T, S>::params(const StepConfig& c) {
     StepParams<T> P;
     P.nx = c.d.nx; P.ny = c.d.ny; P.nz = c.d.nz;
+    P.px = c.d.px;
     P.plane = c.d.plane;
     P.rho_l = (T)c.rho_l; P.rho_g = (T)c.rho_g; P.drho = (T)(c.rho_l - c.rho_g);
     P.inv_nu_l = (T)(1.0 / c.nu_l); P.inv_nu_g = (T)(1.0 / c.nu_g);
@@ -88,7 +89,7 @@ void Launch<T, S>::ghost(int GK, int rule, int64_t ng, const int32_t* node, cons
 
 template <typename T, typename S>
 unsigned Launch<T, S>::flat_blocks(const Dims& d) {
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = (int64_t)d.px * d.ny * d.nz;
     int64_t b = (nn + 255) / 256;
     return (unsigned)(b > 8192 ? 8192 : (b < 1 ? 1 : b));
 }
@@ -227,7 +228,7 @@ void Launch<T, S>::fill_ghost_table(void* out, int64_t n, const int32_t* node, c
 
 template <typename T, typename S>
 int Launch<T, S>::diag_blocks(const Dims& d) {
-    const int64_t nn = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t nn = (int64_t)d.px * d.ny * d.nz;
     int64_t b = (nn + DIAG_THREADS - 1) / DIAG_THREADS;
     return (int)(b > DIAG_MAX_BLOCKS ? DIAG_MAX_BLOCKS : (b < 1 ? 1 : b));
 }
