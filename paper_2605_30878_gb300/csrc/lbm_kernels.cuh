@@ -20,7 +20,9 @@
 //   k_phi    Eq. (phiUpdate): pull B* and sum it at every fluid node
 //
 // Arrays are structure-of-arrays with a plane stride `plane` (a multiple of
-// 64 elements): field[i * plane + node], indexed in 32 bits (Q * plane < 2^31).
+// 64 elements): field[i * plane + node], indexed in 32 bits (Q * plane < 2^31),
+// node = x + px * (y + ny * z) with the row pitch px = nx rounded up to 4 (the
+// padding columns are solid), so rows are 16-byte multiples for TMA copies.
 // Node classes: 0 fluid, 1 ghost (solid boundary node), 2 bulk solid; the step
 // kernels read a per-node 32-bit bounce-back mask derived from them instead.
 #pragma once
