@@ -156,14 +156,19 @@ def recorded_traffic(fluid_nodes):
     return rec["dram_bytes_per_fluid_node"] * fluid_nodes
 
 
-def k_step_bytes_per_fluid_node(Q, D, s, contrast, pop=None):
-    """Algorithmic bytes of one k_step launch per fluid node: pull N (one population
-    array: pop = Q s, or 4 + 2 (Q - 1) with FP16 moving populations) -- the
-    collision needs B only through phi, which k_phi computed --, write N* and B*
-    (2 pop), read phi (s), read the previous u (D s, only with a density contrast),
-    write u (D s) and p (s), read the 4-byte bounce-back mask."""
-    pop = Q * s if pop is None else pop
-    return 3 * pop + s + (D * s if contrast else 0) + D * s + s + 4
+def k_step_bytes_per_fluid_node(Q, D, s, contrast, moving=None, rest=None):
+    """Algorithmic bytes of one k_step launch per fluid node (float arithmetic):
+    pull the Q - 1 moving populations of N (moving bytes each: s, or 2 with FP16
+    storage) -- the deviation form takes the pressure and every moment from
+    them, so the rest population is not read, and the collision needs B only
+    through phi, which k_phi computed --, write N* and B* (rest + (Q - 1)
+    moving bytes each; the rest plane is float), read phi (s), read the previous
+    u (D s, only with a density contrast), write u (D s) and p (s), read the
+    4-byte bounce-back mask."""
+    moving = s if moving is None else moving
+    rest = s if rest is None else rest
+    pop = rest + (Q - 1) * moving
+    return (Q - 1) * moving + 2 * pop + s + (D * s if contrast else 0) + D * s + s + 4
 
 
 def workload(theta, precision, n=N_GRID):
@@ -381,8 +386,7 @@ def run_other_storage(lbm, args, cfg, probe, n_angle, fp64_deg):
     sec = time_domain(d, args.steps, warmup=args.warmup)
     kms = d.profile_steps(max(3, min(args.steps, 60)))
     t_step = kms[1] / max(3, min(args.steps, 60)) * 1e-3
-    pop = 4 + 2 * 18 if prec == lbm.FP16 else 19 * 4
-    kb = k_step_bytes_per_fluid_node(19, 3, 4, True, pop) * fluid
+    kb = k_step_bytes_per_fluid_node(19, 3, 4, True, 2 if prec == lbm.FP16 else 4) * fluid
     peak, peak_kind = hbm_peak()
     d.close()
     da = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
@@ -600,8 +604,7 @@ def run_ours(args):
     t_step = kms[1] / prof_steps * 1e-3
     s, Q, D = 4, 19, 3
     sp = 2 if prec == lbm.FP16 else 4
-    pop = 4 + 2 * (Q - 1) if prec == lbm.FP16 else Q * s
-    kb = k_step_bytes_per_fluid_node(Q, D, s, True, pop) * fluid
+    kb = k_step_bytes_per_fluid_node(Q, D, s, True, sp) * fluid
     achieved = kb / t_step / 1e9
     peak, peak_kind = hbm_peak()
     traffic = recorded_traffic(fluid) if prec == lbm.FP32 else None
@@ -705,7 +708,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "k_step<19,float,%s,contrast>" % ("half" if sp == 2 else "float"),
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "bytes_per_fluid_node": k_step_bytes_per_fluid_node(Q, D, s, True, pop),
+                         "traffic": traffic, "bytes_per_fluid_node": k_step_bytes_per_fluid_node(Q, D, s, True, sp),
                          "avg_launch_ms": t_step * 1e3,
                          "kernel_share": {"ghost": share[0], "step": share[1], "phi": share[2]}},
             "step_bytes_per_fluid_node": bytes_step,

@@ -55,10 +55,11 @@ typedef enum { LBM_GHOST_PRESENT = 0, LBM_GHOST_FAKHARI = 1 } lbm_ghost_rule;
  * the rest state (N_i - chi_i, B_i - chi_i/2), which keeps the small pressure
  * p = p_h/rho of a dense liquid representable.  LBM_FP32_STORE_FP16: float
  * arithmetic, the moving populations' deviations stored in FP16 scaled by
- * 2^16 (N) and 2^7 (B), the rest populations in float; what FP16 rounding drops
- * of a node's moving populations is added to its rest population, so storage
- * conserves mass.  phi, u, p stay float.  Diagnostics reduce in double in every
- * mode. */
+ * 2^16 (N) and 2^7 (B), the rest populations in float; the collision fixes
+ * each node's totals (sum of N_i - chi_i is 0, sum of B_i - chi_i/2 is
+ * phi - 1/2) and the rest populations are written as those totals less the
+ * rounded moving populations, so storage conserves mass.  phi, u, p stay
+ * float.  Diagnostics reduce in double in every mode. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP32_STORE_FP16 = 2 } lbm_precision;
 
 /* Physical and numerical parameters (lattice units).  The model of Sec. II

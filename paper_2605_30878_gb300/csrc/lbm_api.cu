@@ -829,12 +829,16 @@ int32_t lbm_launches_per_step(const lbm_domain* d) { return d ? (d->ng > 0 ? 3 :
 double lbm_bytes_per_fluid_node(const lbm_domain* d) {
     if (!d) return 0.0;
     const double s = (double)d->lay.elem;
-    const double pop = (double)d->lay.rest_elem + (d->lay.Q - 1) * (double)d->lay.pop_elem;   // per node and array
+    const double moving = (d->lay.Q - 1) * (double)d->lay.pop_elem;
+    const double pop = (double)d->lay.rest_elem + moving;   // per node and array
+    // k_step pulls N: the FP64 update follows the literal collision and reads the
+    // rest population, the float updates take every moment from the moving ones
+    const double pull = d->lay.elem == 8 ? pop : moving;
     const int D = d->lay.D;
-    // populations read + written twice over (N, B); phi written (k_phi) and read (k_step);
+    // N* and B* written, B* pulled by k_phi; phi written (k_phi) and read (k_step);
     // u written, and read when the density contrast makes F_visc active; p written; the 4-byte
     // bounce-back mask read by k_step and k_phi
-    return 4.0 * pop + 2.0 * s + (d->contrast ? 2.0 : 1.0) * D * s + s + 8.0;
+    return pull + 3.0 * pop + 2.0 * s + (d->contrast ? 2.0 : 1.0) * D * s + s + 8.0;
 }
 
 int64_t lbm_fluid_nodes(const lbm_domain* d) { return d ? d->n_fluid : 0; }

@@ -66,6 +66,15 @@ struct StepParams {
 constexpr float kScaleN = 65536.0f;
 constexpr float kScaleB = 128.0f;
 
+// float(h) + c, rounded to nearest: one mixed-precision add (sm_100 and
+// later) instead of a conversion and an add; every FP16 value is exact in
+// float, so the result is the same.
+__device__ __forceinline__ float add_f16_f32(__half h, float c) {
+    float r;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(__half_as_ushort(h)), "f"(c));
+    return r;
+}
+
 // Each array holds the rest plane (direction 0) followed by the Q-1 moving
 // planes; rest(p) and moving(p, plane) return typed pointers to the two parts,
 // moving direction d >= 1 lives at moving + (d - 1) * plane.
@@ -82,8 +91,11 @@ template <typename V> struct PlainStore {
     __device__ static V load_moving(const V* m, int idx, float) { return __ldg(m + idx); }
     __device__ static void store_rest(V* r, int idx, V v) { r[idx] = v; }
     __device__ static void store_moving(V* m, int idx, V v, float) { m[idx] = v; }
-    // stores v and returns what storage lost of it (nothing: stored as computed)
-    __device__ static V store_moving_r(V* m, int idx, V v, float) { m[idx] = v; return V(0); }
+    // in storage units: the value itself
+    __device__ static V load_units(const V* m, int idx) { return __ldg(m + idx); }
+    __device__ static void accumulate(const V* m, int idx, V& acc) { acc += __ldg(m + idx); }
+    // stores v; exact storage leaves nothing to account for, acc is untouched
+    __device__ static void store_units(V* m, int idx, V v, V&) { m[idx] = v; }
 };
 template <> struct PopStore<double> : PlainStore<double> {
     static constexpr bool kShift = false, kExact = true;
@@ -106,11 +118,15 @@ template <> struct PopStore<__half> {
     __device__ static void store_moving(__half* m, int idx, float v, float scale) {
         m[idx] = __float2half_rn(v * scale);
     }
-    // stores v and returns the part FP16 rounding dropped, v - stored value
-    __device__ static float store_moving_r(__half* m, int idx, float v, float scale) {
-        const __half h = __float2half_rn(v * scale);
+    // in storage units (value x scale): the step kernels fold the power-of-two
+    // scales into their arithmetic instead of scaling every population
+    __device__ static float load_units(const __half* m, int idx) { return __half2float(__ldg(m + idx)); }
+    __device__ static void accumulate(const __half* m, int idx, float& acc) { acc = add_f16_f32(__ldg(m + idx), acc); }
+    // stores v (already scaled) and adds the value stored to acc
+    __device__ static void store_units(__half* m, int idx, float v, float& acc) {
+        const __half h = __float2half_rn(v);
         m[idx] = h;
-        return v - __half2float(h) * (1.0f / scale);
+        acc = add_f16_f32(h, acc);
     }
 };
 
@@ -314,13 +330,20 @@ __device__ __forceinline__ void phi_node(const StepParams<T>& P, const S* __rest
     const int pl = (int)P.plane;
     using PS = PopStore<S>;
     const auto* mv = PS::moving(Bst, pl);
-    T s = (T)PS::load_rest(PS::rest(Bst), node);
+    // FP64 sums in lattice order, as Eq. (phiUpdate) is written.  The
+    // deviation forms sum the moving populations first, in storage units, and
+    // add the rest population last: with FP16 storage the moving values lie on
+    // a grid coarse enough for their float sum to be exact, so the node's color
+    // comes back as k_step wrote it.
+    const T rest = (T)PS::load_rest(PS::rest(Bst), node);
+    T s = PS::kShift ? T(0) : rest;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int idx = ((m >> i) & 1u) ? (L::opp(i) - 1) * pl + node
                                         : (i - 1) * pl + node + W.off(-L::cx(i), -L::cy(i), -L::cz(i));
-        s += (T)PS::load_moving(mv, idx, kScaleB);
+        PS::accumulate(mv, idx, s);
     }
+    if (PS::kShift) s = rest + (PS::kExact ? s : s * T(1.0 / kScaleB));
     // stored deviations B_i - chi_i/2 sum to phi - 1/2
     phi[node] = PS::kShift ? T(0.5) + s : s;
 }
@@ -482,30 +505,14 @@ __device__ __forceinline__ void node_update_literal(const StepParams<double>& P,
     }
 }
 
-// Pull the post-streaming populations N of fluid node (x, y, z) with mask m
-// (bounce-back where x - c_i is solid).  B enters the collision only through
-// phi = sum B, which k_phi computed.  Full values for FP64 storage,
-// deviations N_i - chi_i otherwise.
-template <int Q, typename T, typename S>
-__device__ __forceinline__ void pull_node(const StepParams<T>& P, const S* __restrict__ Nin, uint32_t m, int node,
-                                          int x, int y, int z, T (&N)[Q]) {
-    using L = Lattice<Q>;
-    using PS = PopStore<S>;
-    const Wrap Wr(x, y, z, P.nx, P.ny, P.nz, P.px);
-    const int pl = (int)P.plane;
-    N[0] = (T)PS::load_rest(PS::rest(Nin), node);
-    const auto* mv = PS::moving(Nin, pl);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int idx = ((m >> i) & 1u) ? (L::opp(i) - 1) * pl + node
-                                        : (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i));
-        N[i] = (T)PS::load_moving(mv, idx, kScaleN);
-    }
-}
-
-// The same pull issued before the node's mask is known: every direction by
-// streaming (x - c_i always lies in the grid), then the directions whose
-// neighbour is not fluid are read again from the node's own opposite slot.
+// The pull of the post-streaming populations N of node (x, y, z), issued
+// before the node's mask is known: every direction by streaming (x - c_i
+// always lies in the grid), then the directions whose neighbour is not fluid
+// are read again from the node's own opposite slot.  B enters the collision
+// only through phi = sum B, which k_phi computed.  Values come in storage
+// units (times kScaleN with FP16 storage).  Only the literal FP64 update reads
+// the rest population: in the deviation form the pressure and every moment
+// come from the moving populations (Eq. pressureUpdate), so N[0] is not read.
 template <int Q, typename T, typename S>
 __device__ __forceinline__ void pull_streaming(const StepParams<T>& P, const S* __restrict__ Nin, int node, int x,
                                                int y, int z, T (&N)[Q]) {
@@ -513,11 +520,11 @@ __device__ __forceinline__ void pull_streaming(const StepParams<T>& P, const S* 
     using PS = PopStore<S>;
     const Wrap Wr(x, y, z, P.nx, P.ny, P.nz, P.px);
     const int pl = (int)P.plane;
-    N[0] = (T)PS::load_rest(PS::rest(Nin), node);
+    N[0] = PS::kShift ? T(0) : (T)PS::load_rest(PS::rest(Nin), node);
     const auto* mv = PS::moving(Nin, pl);
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        N[i] = (T)PS::load_moving(mv, (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i)), kScaleN);
+        N[i] = (T)PS::load_units(mv, (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i)));
 }
 template <int Q, typename T, typename S>
 __device__ __forceinline__ void pull_bounce_back(const StepParams<T>& P, const S* __restrict__ Nin, uint32_t m,
@@ -528,7 +535,7 @@ __device__ __forceinline__ void pull_bounce_back(const StepParams<T>& P, const S
     const auto* mv = PS::moving(Nin, pl);
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        if ((m >> i) & 1u) N[i] = (T)PS::load_moving(mv, (L::opp(i) - 1) * pl + node, kScaleN);
+        if ((m >> i) & 1u) N[i] = (T)PS::load_units(mv, (L::opp(i) - 1) * pl + node);
 }
 
 // One fluid node of the step: pulled populations N, the block's halo tile.
@@ -560,19 +567,21 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
         if (kPairs) {
             if (L::opp(i) < i) continue;
             const int hp = hc + Tl::off(cx, cy, cz), hm = hc - Tl::off(cx, cy, cz);
+            // each difference enters every component it feeds with one
+            // multiply-add by the constant c_ia w_i
             const T pp = s_phi[hp], pm = s_phi[hm];
-            const T dphi = wi * (pp - pm);
-            if (cx) gp[0] += T(cx) * dphi;
-            if (cy) gp[1] += T(cy) * dphi;
-            if (cz) gp[2] += T(cz) * dphi;
+            const T dphi = pp - pm;
+            if (cx) gp[0] += (T(cx) * wi) * dphi;
+            if (cy) gp[1] += (T(cy) * wi) * dphi;
+            if (cz) gp[2] += (T(cz) * wi) * dphi;
             lsum += wi * ((pp - phi) + (pm - phi));
             if (CONTRAST) {
 #pragma unroll
                 for (int bb = 0; bb < D; ++bb) {
-                    const T dub = wi * (s_u[bb * Tl::HN + hp] - s_u[bb * Tl::HN + hm]);
-                    if (cx) du[0][bb] += T(cx) * dub;
-                    if (cy) du[1][bb] += T(cy) * dub;
-                    if (cz) du[2][bb] += T(cz) * dub;
+                    const T dub = s_u[bb * Tl::HN + hp] - s_u[bb * Tl::HN + hm];
+                    if (cx) du[0][bb] += (T(cx) * wi) * dub;
+                    if (cy) du[1][bb] += (T(cy) * wi) * dub;
+                    if (cz) du[2][bb] += (T(cz) * wi) * dub;
                 }
             }
         } else {
@@ -627,38 +636,33 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     const T tau = T(0.5) + T(3) * nu;
 
     // force-free velocity, moments and the pressure of this step (Eq. pressureUpdate)
+    static_assert(kPairs && kShift, "float arithmetic runs on deviations, summed over +/- pairs");
     T u0[3] = {T(0), T(0), T(0)};
     T sum_moving = T(0);
     T Pxx = T(0), Pyy = T(0), Pzz = T(0), Pxy = T(0), Pxz = T(0), Pyz = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        if (kPairs) {
-            // odd moments from N_i - N_opp, even ones from N_i + N_opp
-            if (L::opp(i) < i) continue;
-            const T sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
-            sum_moving += sp;
-            if (cx) { u0[0] += T(cx) * dp; Pxx += sp; }
-            if (cy) { u0[1] += T(cy) * dp; Pyy += sp; }
-            if (cz) { u0[2] += T(cz) * dp; Pzz += sp; }
-            if (cx * cy) Pxy += T(cx * cy) * sp;
-            if (cx * cz) Pxz += T(cx * cz) * sp;
-            if (cy * cz) Pyz += T(cy * cz) * sp;
-        } else {
-            sum_moving += N[i];
-            if (cx > 0) { u0[0] += N[i]; Pxx += N[i]; }
-            if (cx < 0) { u0[0] -= N[i]; Pxx += N[i]; }
-            if (cy > 0) { u0[1] += N[i]; Pyy += N[i]; }
-            if (cy < 0) { u0[1] -= N[i]; Pyy += N[i]; }
-            if (cz > 0) { u0[2] += N[i]; Pzz += N[i]; }
-            if (cz < 0) { u0[2] -= N[i]; Pzz += N[i]; }
-            if (cx * cy > 0) Pxy += N[i];
-            if (cx * cy < 0) Pxy -= N[i];
-            if (cx * cz > 0) Pxz += N[i];
-            if (cx * cz < 0) Pxz -= N[i];
-            if (cy * cz > 0) Pyz += N[i];
-            if (cy * cz < 0) Pyz -= N[i];
-        }
+        // odd moments from N_i - N_opp, even ones from N_i + N_opp
+        if (L::opp(i) < i) continue;
+        const T sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
+        sum_moving += sp;
+        if (cx) { u0[0] += T(cx) * dp; Pxx += sp; }
+        if (cy) { u0[1] += T(cy) * dp; Pyy += sp; }
+        if (cz) { u0[2] += T(cz) * dp; Pzz += sp; }
+        if (cx * cy) Pxy += T(cx * cy) * sp;
+        if (cx * cz) Pxz += T(cx * cz) * sp;
+        if (cy * cz) Pyz += T(cy * cz) * sp;
+    }
+    // FP16 storage: N came in storage units (times 2^16); the moments are linear
+    // in N, so they are scaled back once (exactly, a power of two)
+    constexpr bool kUnits = !PS::kExact;
+    if constexpr (kUnits) {
+        constexpr T r = T(1.0 / kScaleN);
+        sum_moving *= r;
+        Pxx *= r; Pyy *= r; Pzz *= r; Pxy *= r; Pxz *= r; Pyz *= r;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u0[a] *= r;
     }
     // sum_{i>0} chi_i = 1 - chi_0: with deviations the chi part is already gone
     const T pres_base = kShift ? sum_moving * T(1.0 / 3.0) : (sum_moving - (T(1) - P.chi[0])) * T(1.0 / 3.0);
@@ -694,7 +698,12 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     const T p = (pres_base - T(0.5 * w0) * uu) * inv_1mw0;
 
     // collision: traceless second moments of N - Neq, with sum Neq c c = (c2chi + p) I + u u
-    const T omega1 = T(1) - rcp(tau);        // 1 - s_nu
+    // Populations are produced in storage units: times sN (N) and sB (B), 2^16
+    // and 2^7 with FP16 storage, else 1.  Being powers of two, the scales fold
+    // into the per-node factors below (omega1, the weights, phi, kseg) and the
+    // scaled values round exactly as the unscaled ones would.
+    constexpr T sN = kUnits ? T(kScaleN) : T(1), sB = kUnits ? T(kScaleB) : T(1);
+    const T omega1 = kUnits ? (T(1) - rcp(tau)) * sN : T(1) - rcp(tau);        // 1 - s_nu
     T A0, A1, Axy, Axz, Ayz;
     if (D == 2) {
         A0 = omega1 * ((Pxx - Pyy) - (u[0] * u[0] - u[1] * u[1])) * T(0.25);     // m7 . f / |m7|^2
@@ -712,32 +721,37 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     // segregation: n_phi = grad phi / max(|grad phi|, 1e-6)
     const T inv_gn = inv_norm_floor(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2], T(1e-6));
     const T kseg = P.two_over_W * phi * (T(1) - phi) * inv_gn;
+    const T ksegB = kUnits ? kseg * sB : kseg;                       // recoloring in B's units
+    const T phiB = kUnits ? phi * (sB / sN) : phi;                   // phi N*, from N's units to B's
+    const T phmB = kUnits ? (phi - T(0.5)) * sB : phi - T(0.5);
     const T three_p = T(3) * p;
     const T halfF = T(1.5) * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
     const T base0 = T(3) * u[0], base1 = T(3) * u[1], base2 = T(3) * u[2];
     const T common = three_p - T(1.5) * uu;
 
-    auto* __restrict__ Nrest = PS::rest(b.Nout);
-    auto* __restrict__ Brest = PS::rest(b.Bout);
+    // u and p first: neither is needed by the populations below
+#pragma unroll
+    for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
+    b.p[node] = p;
+    if (!(uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
+
     auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
     auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
     // rest direction: no forcing, no stress projection, no recoloring (c_0 = 0)
-    const T nst0 = (kShift ? T(0) : P.chi[0]) - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
-    const T bst0 = kShift ? phi * nst0 + (phi - T(0.5)) * P.chi[0] : phi * nst0;
     if constexpr (PS::kExact) {
-        PS::store_rest(Nrest, node, nst0);
-        PS::store_rest(Brest, node, bst0);
+        const T nst0 = T(0) - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
+        PS::store_rest(PS::rest(b.Nout), node, nst0);
+        PS::store_rest(PS::rest(b.Bout), node, phi * nst0 + (phi - T(0.5)) * P.chi[0]);
     }
-    // What storage drops of the moving populations (FP16 rounding) is added to
-    // the node's rest population, kept in float: the stored N* and B* of a node
-    // then sum to what the collision and segregation produced, so storage
-    // rounding moves no mass between phases or out of the domain.
-    T lostN = T(0), lostB = T(0);
+    // sums of the moving populations as stored (FP16 storage)
+    T sumN = T(0), sumB = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
+        // direction i and its opposite share the even part and flip the odd part
+        if (L::opp(i) < i) continue;
+        const int o = L::opp(i);
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const T wi = T(L::w(i));
-        const T chi_i = kShift ? T(0) : P.chi[i];      // the rest-state part carried in N
+        const T wi = T(L::w(i)), wiN = T(L::w(i)) * sN;
         T proj;
         if (D == 2) {
             proj = T(cx * cx - cy * cy) * A0 + T(cx * cy) * Axy;
@@ -750,36 +764,28 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
         if (cx) { cu3 += T(cx) * base0; cF += T(cx) * F[0]; cg += T(cx) * gp[0]; }
         if (cy) { cu3 += T(cy) * base1; cF += T(cy) * F[1]; cg += T(cy) * gp[1]; }
         if (cz) { cu3 += T(cz) * base2; cF += T(cz) * F[2]; cg += T(cz) * gp[2]; }
-        const T rc = kseg * cg * (P.chi[i] + wi * three_p);     // recoloring, odd in c
-        if (kPairs) {
-            // direction i and its opposite share the even part and flip the odd part
-            if (L::opp(i) < i) continue;
-            const int o = L::opp(i);
-            const T even = chi_i + wi * (common + T(0.5) * cu3 * cu3) + proj;
-            const T odd = wi * (cu3 + halfF * cF);
-            const T ni = even + odd, no = even - odd;
-            const T shift_b = kShift ? (phi - T(0.5)) * P.chi[i] : T(0);
-            lostN += PS::store_moving_r(Nmov, (i - 1) * pl + node, ni, kScaleN);
-            lostN += PS::store_moving_r(Nmov, (o - 1) * pl + node, no, kScaleN);
-            lostB += PS::store_moving_r(Bmov, (i - 1) * pl + node, phi * ni + shift_b + rc, kScaleB);
-            lostB += PS::store_moving_r(Bmov, (o - 1) * pl + node, phi * no + shift_b - rc, kScaleB);
-        } else {
-            const T neq = chi_i + wi * (common + cu3 + T(0.5) * cu3 * cu3);
-            const T nst = neq + wi * halfF * cF + proj;
-            // B* = phi N* + recolor; stored as B* - chi_i/2 = phi dN* + (phi - 1/2) chi_i + recolor
-            const T bst = (kShift ? phi * nst + (phi - T(0.5)) * P.chi[i] : phi * nst) + rc;
-            lostN += PS::store_moving_r(Nmov, (i - 1) * pl + node, nst, kScaleN);
-            lostB += PS::store_moving_r(Bmov, (i - 1) * pl + node, bst, kScaleB);
-        }
+        const T rc = ksegB * cg * (P.chi[i] + wi * three_p);     // recoloring, odd in c
+        const T even = wiN * (common + T(0.5) * cu3 * cu3) + proj;
+        const T odd = wiN * (cu3 + halfF * cF);
+        const T ni = even + odd, no = even - odd;
+        // B* = phi N* + recolor, stored as B* - chi_i/2 = phi dN* + (phi - 1/2) chi_i + recolor
+        const T shift_b = phmB * P.chi[i];
+        PS::store_units(Nmov, (i - 1) * pl + node, ni, sumN);
+        PS::store_units(Nmov, (o - 1) * pl + node, no, sumN);
+        PS::store_units(Bmov, (i - 1) * pl + node, phiB * ni + shift_b + rc, sumB);
+        PS::store_units(Bmov, (o - 1) * pl + node, phiB * no + shift_b - rc, sumB);
     }
     if constexpr (!PS::kExact) {
-        PS::store_rest(Nrest, node, nst0 + lostN);
-        PS::store_rest(Brest, node, bst0 + lostB);
+        // The collision keeps each node's population totals: sum_i (N*_i - chi_i)
+        // = 0 for any N, u, p and F (the equilibrium sums to sum chi = 1; the
+        // stress projection and the forcing have no zeroth moment), and
+        // sum_i (B*_i - chi_i/2) = phi - 1/2 (the recoloring is odd in c).  The
+        // float rest populations are written as those totals less the rounded
+        // moving populations, so FP16 rounding moves no mass between the phases
+        // or out of the domain.
+        PS::store_rest(PS::rest(b.Nout), node, -sumN * T(1.0 / kScaleN));
+        PS::store_rest(PS::rest(b.Bout), node, (phi - T(0.5)) - sumB * T(1.0 / kScaleB));
     }
-#pragma unroll
-    for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
-    b.p[node] = p;
-    if (!(uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
     }
 }
 
@@ -845,11 +851,12 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
 
 // Resident blocks per SM the step kernels are compiled for (registers per
 // thread <= 65536 / (256 * blocks)): measured on the 192^3 bench case, FP32
-// runs best at 5 (48 registers, no spills), FP16 storage at 6 (40 registers);
+// and FP16 storage run best at 5 (48 registers, no spills; FP16 storage at 6
+// blocks spills at 40 registers and runs 1.5% slower, at 4 it is 4% slower);
 // FP64 keeps the compiler's choice.
 template <typename T, typename S> struct StepOccupancy { static constexpr int kBlocks = 1; };
 template <> struct StepOccupancy<float, float> { static constexpr int kBlocks = 5; };
-template <> struct StepOccupancy<float, __half> { static constexpr int kBlocks = 6; };
+template <> struct StepOccupancy<float, __half> { static constexpr int kBlocks = 5; };
 // the same register budget for other block sizes
 template <typename T, typename S, int THREADS>
 constexpr int step_min_blocks() {

@@ -3,9 +3,26 @@
 // Launch<T, S> (and so every kernel) once each.
 #pragma once
 
+#include <cmath>
+
 #include "lbm_launch.cuh"
 
 namespace lbmgpu {
+
+// chi for float arithmetic: the moving values on a grid of 2^-24 and chi_0 =
+// 1 minus their sum, a multiple of 2^-24 below 1 and so exact in float, so the
+// float values sum to exactly 1.  sum chi = 1 is what makes the collision keep
+// each node's color (sum_i B*_i = phi sum_i chi_i); values rounded one by one
+// sum to 1 + delta (delta ~ 3e-8 from chi_0 alone) and move (phi - 1/2) delta
+// of color per node and step, a drift of 1e-4 of a drop's color in 300 steps.
+inline void chi_for_float(const double* chi, double* out) {
+    double rest = 1.0;
+    for (int i = 1; i < 19; ++i) {
+        out[i] = std::ldexp(std::nearbyint(std::ldexp(chi[i], 24)), -24);
+        rest -= out[i];
+    }
+    out[0] = rest;
+}
 
 template <typename T, typename S>
 StepParams<T> Launch<T, S>::params(const StepConfig& c) {
@@ -20,7 +37,10 @@ StepParams<T> Launch<T, S>::params(const StepConfig& c) {
     P.nu_l = (T)c.nu_l; P.nu_g = (T)c.nu_g;
     P.k48W = (T)(48.0 / c.W); P.k3W2 = (T)(1.5 * c.W); P.two_over_W = (T)(2.0 / c.W);
     for (int a = 0; a < 3; ++a) P.g[a] = (T)c.g[a];
-    for (int i = 0; i < 19; ++i) P.chi[i] = (T)c.chi[i];
+    double chi[19];
+    if (sizeof(T) == 4) chi_for_float(c.chi, chi);
+    else std::memcpy(chi, c.chi, sizeof(chi));
+    for (int i = 0; i < 19; ++i) P.chi[i] = (T)chi[i];
     P.c2chi = (T)c.c2chi;
     P.exp_eps = (T)c.exp_eps;
     return P;
@@ -126,7 +146,10 @@ void Launch<T, S>::build_mask(const StepConfig& c, const uint8_t* cls, uint32_t*
 template <typename T, typename S>
 double Launch<T, S>::storage_base(const StepConfig& c, int i, bool is_b) {
     if (!PopStore<S>::kShift) return 0.0;
-    return is_b ? 0.5 * c.chi[i] : c.chi[i];
+    double chi[19];                     // the deviations are taken from the chi the kernels use
+    if (sizeof(T) == 4) chi_for_float(c.chi, chi);
+    else std::memcpy(chi, c.chi, sizeof(chi));
+    return is_b ? 0.5 * chi[i] : chi[i];
 }
 
 template <typename T, typename S>

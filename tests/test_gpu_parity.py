@@ -236,6 +236,20 @@ def test_tiny_and_solid_free_domains(shape, Q):
     assert g.launches_per_step() == 2
 
 
+@pytest.mark.parametrize("precision,want", [(lbm.FP32, 344.0), (lbm.FP16, 200.0), (lbm.FP64, 688.0)])
+def test_algorithmic_bytes_per_fluid_node(precision, want):
+    """Whole-step bytes per fluid node, D3Q19 with a density contrast.  Float
+    arithmetic: k_step pulls the 18 moving N (the rest population enters no
+    moment of the deviation form), N* and B* are written and B* pulled by k_phi
+    (3 x 19 values, the rest plane float), phi written and read, u read and
+    written, p written, the mask read twice.  FP32: 72 + 228 + 8 + 24 + 4 + 8.
+    FP16 storage: 36 + 3 x 40 + 8 + 24 + 4 + 8.  FP64 reads the rest
+    population too: 152 + 456 + 16 + 48 + 8 + 8."""
+    cfg = small_3d()
+    g = lbm.Domain(dict(cfg["params"], precision=precision), cfg["solid"], cfg["ghosts"])
+    assert g.bytes_per_fluid_node() == want
+
+
 def test_neutral_angle_and_flat_wall_fp64():
     """theta = 90 deg (eps = 0, phi_G = phi_F) on flat walls in a non-periodic channel."""
     shape = (1, 24, 40)
@@ -265,6 +279,31 @@ def test_mass_conservation_and_determinism_fp64():
         assert abs(d1["pop_sum"] - d1["n_fluid"]) < 1e-12 * d1["n_fluid"]
         runs.append((g.read("N"), g.read("B")))
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16])
+def test_mass_conservation_float_storage(precision):
+    """Color (sum phi) and population (sum N = fluid nodes) totals over 300
+    steps.  Streaming permutes stored values and the collision fixes each
+    node's totals (sum_i B*_i = phi sum chi, sum_i N*_i = sum chi, the float
+    chi summing to exactly 1).  FP16 storage writes the float rest populations
+    as those totals less the rounded moving populations; the moving values lie
+    on a coarse grid, their float sums are exact, and the color comes back to
+    ~5e-9.  FP32 writes all 19 values from their formulas: each node's total
+    carries ~2e-9 of float rounding per step that does not average out, 3e-5
+    to 4e-5 of the color here (1.1e-4 with chi rounded one by one).  A wrong
+    node total would move O(1e-2) or more per step."""
+    cfg = small_3d(rho_ratio=10.0)
+    g = lbm.Domain(dict(cfg["params"], precision=precision), cfg["solid"], cfg["ghosts"])
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    g.step(1)
+    d0 = g.diagnostics()
+    g.step(300)
+    d1 = g.diagnostics()
+    dphi = abs(d1["phi_sum"] / d0["phi_sum"] - 1)
+    dpop = abs(d1["pop_sum"] / d1["n_fluid"] - 1)
+    print("precision", precision, "phi_sum drift %.2e, pop_sum - fluid %.2e" % (dphi, dpop))
+    assert dphi < {lbm.FP32: 1e-4, lbm.FP16: 1e-6}[precision] and dpop < 1e-6
 
 
 def test_instability_is_reported_not_faulted():

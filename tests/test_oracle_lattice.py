@@ -165,6 +165,31 @@ def test_collision_conserves_and_forces(Q):
 
 
 @pytest.mark.parametrize("Q", [9, 19])
+def test_post_collision_total_is_fixed(Q):
+    """sum_i N*_i = sum chi = 1 for any N, u, p and F, not only the u and p of
+    N: the equilibrium's zeroth moment is sum chi (its p and u^2 terms in the
+    moving directions cancel against the rest population's), the stress
+    projection is traceless and the forcing has no zeroth moment.  The
+    recoloring term of Eq. (segragationStepBlue) is odd in c_i, chi and w are
+    even, so sum_i B*_i = phi sum_i N*_i as well.  FP16 population storage
+    writes each node's float rest populations from these two totals."""
+    rng = np.random.default_rng(17)
+    D = 2 if Q == 9 else 3
+    t = oracle.lattice_tables(Q, MPHI)
+    c, w, chi, opp = t["c"], t["w"], t["chi"], np.asarray(t["opp"])
+    assert abs(chi.sum() - 1) < 1e-15
+    assert np.array_equal(chi[opp], chi) and np.array_equal(w[opp], w) and np.array_equal(c[opp], -c)
+    for _ in range(50):
+        N = chi + rng.normal(0, 0.05, Q)
+        u = np.zeros(3)
+        u[:D] = rng.normal(0, 0.05, D)
+        F = np.zeros(3)
+        F[:D] = rng.normal(0, 1e-3, D)
+        Ns = oracle.collide(Q, N, u, rng.normal(0, 0.01), F, rng.uniform(0.5, 1000), rng.uniform(0.51, 2), MPHI)
+        assert abs(Ns.sum() - 1) < 1e-14
+
+
+@pytest.mark.parametrize("Q", [9, 19])
 def test_collision_at_tau_one_is_bgk(Q):
     """At tau = 1 every rate is 1 and Eq. (MRTCOLL) reduces to N* = Neq + F_i / 2."""
     rng = np.random.default_rng(8)
