@@ -143,9 +143,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(fluid_nodes):
-    """DRAM bytes per k_step launch from the committed ncu summary, scaled to
-    this launch's fluid nodes; None if the kernel source changed since."""
+def recorded_traffic(fluid_nodes, fp16=False):
+    """DRAM bytes per k_step launch from the committed ncu summary (FP32, or
+    FP16 population storage), scaled to this launch's fluid nodes; None if the
+    kernel source changed since."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
@@ -153,6 +154,10 @@ def recorded_traffic(fluid_nodes):
         return None
     if rec.get("kernel_hash") != kernel_source_hash():
         return None
+    if fp16:
+        rec = rec.get("k_step_fp16_storage")
+        if rec is None:
+            return None
     return rec["dram_bytes_per_fluid_node"] * fluid_nodes
 
 
@@ -398,6 +403,7 @@ def run_other_storage(lbm, args, cfg, probe, n_angle, fp64_deg):
     n = cfg["params"]["nx"]
     return {"storage": key, "value": n ** 3 / sec / 1e6, "unit": "MLUPS", "ms_per_step": sec * 1e3,
             "k_step": {"avg_launch_ms": t_step * 1e3, "bytes_per_fluid_node": kb / fluid,
+                       "traffic": recorded_traffic(fluid, fp16=prec == lbm.FP16),
                        "achieved_gbs": kb / t_step / 1e9, "frac": kb / t_step / 1e9 / peak, "peak_kind": peak_kind},
             "contact_angle_deg": deg, "vs_fp64_deg": abs(deg - fp64_deg) if fp64_deg is not None else None}
 
@@ -607,7 +613,7 @@ def run_ours(args):
     kb = k_step_bytes_per_fluid_node(Q, D, s, True, sp) * fluid
     achieved = kb / t_step / 1e9
     peak, peak_kind = hbm_peak()
-    traffic = recorded_traffic(fluid) if prec == lbm.FP32 else None
+    traffic = recorded_traffic(fluid, fp16=prec == lbm.FP16)
     share = kms / kms.sum()
     launches = dom.launches_per_step()
     bytes_step = dom.bytes_per_fluid_node()

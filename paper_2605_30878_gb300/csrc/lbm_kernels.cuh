@@ -729,11 +729,16 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     const T base0 = T(3) * u[0], base1 = T(3) * u[1], base2 = T(3) * u[2];
     const T common = three_p - T(1.5) * uu;
 
-    // u and p first: neither is needed by the populations below
+    // u and p: FP16 storage writes them before the populations, which frees
+    // their registers for the stored sums (no spills in the batched kernels);
+    // FP32 writes them last, measured 0.7% faster
+    auto store_u_p = [&]() {
 #pragma unroll
-    for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
-    b.p[node] = p;
-    if (!(uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
+        for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
+        b.p[node] = p;
+        if (!(uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
+    };
+    if constexpr (!PS::kExact) store_u_p();
 
     auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
     auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
@@ -786,6 +791,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
         PS::store_rest(PS::rest(b.Nout), node, -sumN * T(1.0 / kScaleN));
         PS::store_rest(PS::rest(b.Bout), node, (phi - T(0.5)) - sumB * T(1.0 / kScaleB));
     }
+    if constexpr (PS::kExact) store_u_p();
     }
 }
 

@@ -112,9 +112,10 @@ def cylinder_oracle():
 @pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
 def test_contact_angle_per_storage_precision(cylinder_oracle, precision):
     """Contact angle of the equilibrated drop on the cylinder against the FP64
-    oracle after 16000 steps of spreading: FP64 1.2e-12 deg, FP32 0.025 deg, FP16
-    storage 1.6e-3 deg (FP16 keeps 11 significant bits of the stored deviations;
-    what rounding drops goes to the float rest population).  Bound: 0.5 deg."""
+    oracle after 16000 steps of spreading, measured: FP64 1.2e-12 deg, FP32
+    0.020 deg, FP16 storage 3.0e-3 deg (FP16 keeps 11 significant bits of the
+    stored deviations; the float rest populations take the node totals less
+    the rounded moving ones).  Bound: 0.5 deg."""
     cfg, do = cylinder_oracle
     g = lbm.Domain(dict(cfg["params"], precision=precision), cfg["solid"], cfg["ghosts"])
     g.init_droplet(cfg["drop_center"], cfg["R0"])
@@ -152,7 +153,7 @@ def test_laplace_pressure_and_spurious_current_per_storage_precision(laplace_ora
     dp_o, dp_g = do["p_in"] - do["p_out"], dg["p_in"] - dg["p_out"]
     print("precision", precision, "Laplace dP %.6e vs oracle %.6e (rel %.2e)" % (dp_g, dp_o, abs(dp_g / dp_o - 1)),
           "max|u| %.3e vs %.3e" % (dg["max_u"], do["max_u"]))
-    # measured: FP64 2.5e-10, FP32 9.8e-4, FP16 storage 4.5e-4 relative
+    # measured: FP64 2.5e-10, FP32 1.0e-3, FP16 storage 5.0e-4 relative
     bound = {lbm.FP64: 1e-9, lbm.FP32: 5e-3, lbm.FP16: 5e-3}[precision]
     assert abs(dp_g / dp_o - 1) < bound
     assert dg["max_u"] < 1e-6
