@@ -95,7 +95,10 @@ typedef struct {
 } lbm_ghost;
 
 /* Optional analytic description of the solid surface, used only by
- * lbm_diagnostics to measure the contact angle and the apex height. */
+ * lbm_diagnostics to measure the contact angle and the apex height.  Each
+ * phi = 1/2 interface point is taken at its nearest periodic image from
+ * center, so the drop must lie within half a box of it in every periodic
+ * direction. */
 typedef struct {
     int32_t kind;           /* 0 none, 1 circle (2D) / sphere (3D), 2 plane */
     int32_t reserved;
