@@ -38,7 +38,7 @@ typedef enum {
     LBM_ERR_OOM = -2,          /* device allocation failed or workspace too small */
     LBM_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     LBM_ERR_UNSTABLE = -4,     /* a step produced a non-finite velocity or color */
-    LBM_ERR_TIMEOUT = -5,      /* reserved for bounded device waits */
+    LBM_ERR_TIMEOUT = -5,      /* a bounded device wait gave up (a step kernel's TMA halo copy did not complete) */
     LBM_ERR_UNSUPPORTED = -6   /* valid request the library does not implement */
 } lbm_status;
 
