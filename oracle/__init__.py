@@ -81,6 +81,7 @@ def lib():
         L.orc_macro.argtypes = [C.c_int, C.c_double, _dp, _dp, C.c_double, _dp, _dp]
         L.orc_collide.argtypes = [C.c_int, C.c_double, _dp, _dp, C.c_double, _dp, C.c_double,
                                   C.c_double, _dp]
+        L.orc_segregate.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, _dp, C.c_double, _dp, _dp]
         L.orc_ghost_rule.argtypes = [C.c_double, C.c_double]
         L.orc_ghost_rule.restype = C.c_double
         L.orc_ghost_rule_fakhari.argtypes = [C.c_double, C.c_double]
@@ -155,6 +156,15 @@ def collide(lattice, N, u, p, F, rho, tau, M_phi=0.02):
     out = np.zeros(lattice)
     lib().orc_collide(lattice, M_phi, _d(np.ascontiguousarray(N, dtype=np.float64)), _d(_vec3(u)), p,
                       _d(_vec3(F)), rho, tau, _d(out))
+    return out
+
+
+def segregate(lattice, Nst, phi, gphi, p, W=4.0, M_phi=0.02):
+    """Eq. (segragationStepBlue) at one node: the post-collision color
+    populations B* from N*, phi, grad phi and the pressure p."""
+    out = np.zeros(lattice)
+    lib().orc_segregate(lattice, M_phi, W, phi, _d(_vec3(gphi)), p,
+                        _d(np.ascontiguousarray(Nst, dtype=np.float64)), _d(out))
     return out
 
 

@@ -351,6 +351,22 @@ static void coords(const orc_sim* s, int64_t node, double r[3]) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Eq. (segragationStepBlue) with N^{eq,u=0}: B*_i = phi N*_i + (2/W)(c_i . n_phi)
+ * phi (1 - phi) N^{eq,u=0}_i, n_phi = grad phi / max(|grad phi|, 1e-6) */
+static void segregate(const lattice_t* L, double W, double phi, const double gphi[3], double p,
+                      const double* Nst, double* Bst) {
+    int Q = L->Q;
+    double gn = sqrt(gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2]);
+    double n[3];
+    for (int a = 0; a < 3; ++a) n[a] = gphi[a] / (gn > NPHI_FLOOR ? gn : NPHI_FLOOR);
+    double neq0[QMAX], zero[3] = {0, 0, 0};
+    equilibrium(L, zero, p, neq0);
+    for (int i = 0; i < Q; ++i) {
+        double cn = L->c[i][0] * n[0] + L->c[i][1] * n[1] + L->c[i][2] * n[2];
+        Bst[i] = phi * Nst[i] + 2.0 * (cn / W) * phi * (1.0 - phi) * neq0[i];
+    }
+}
+
 /* one node: stencils, forces, macroscopic fields, collision, segregation */
 /* ------------------------------------------------------------------ */
 
@@ -412,16 +428,7 @@ static void collide_node(const orc_sim* s, const double* phif, int64_t x, double
     macro(L, N, F, rho, u, &p);
     collide(L, N, u, p, F, rho, tau, Nst);
 
-    /* Eq. (segragationStepBlue) with N^{eq,u=0}; n_phi = grad phi / max(|grad phi|, 1e-6) */
-    double gn = sqrt(gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2]);
-    double n[3];
-    for (int a = 0; a < 3; ++a) n[a] = gphi[a] / (gn > NPHI_FLOOR ? gn : NPHI_FLOOR);
-    double neq0[QMAX], zero[3] = {0, 0, 0};
-    equilibrium(L, zero, p, neq0);
-    for (int i = 0; i < Q; ++i) {
-        double cn = L->c[i][0] * n[0] + L->c[i][1] * n[1] + L->c[i][2] * n[2];
-        Bst[i] = phi * Nst[i] + 2.0 * (cn / P->W) * phi * (1.0 - phi) * neq0[i];
-    }
+    segregate(L, P->W, phi, gphi, p, Nst, Bst);
     *p_out = p;
 }
 
@@ -927,4 +934,11 @@ void orc_collide(int lattice, double M_phi, const double* N, const double u[3], 
     lattice_t L;
     build_lattice(&L, lattice, M_phi, 0);
     collide(&L, N, u, p, F, rho, tau, Nst);
+}
+
+void orc_segregate(int lattice, double M_phi, double W, double phi, const double gphi[3], double p,
+                   const double* Nst, double* Bst) {
+    lattice_t L;
+    build_lattice(&L, lattice, M_phi, 0);
+    segregate(&L, W, phi, gphi, p, Nst, Bst);
 }

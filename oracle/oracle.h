@@ -84,6 +84,9 @@ void   orc_macro(int lattice, double M_phi, const double* N, const double F[3], 
                  double u[3], double* p);
 void   orc_collide(int lattice, double M_phi, const double* N, const double u[3], double p,
                    const double F[3], double rho, double tau, double* Nst);
+/* Eq. (segragationStepBlue) at one node: B* from N*, phi, grad phi and p (W the interface width) */
+void   orc_segregate(int lattice, double M_phi, double W, double phi, const double gphi[3], double p,
+                     const double* Nst, double* Bst);
 double orc_ghost_rule(double phiF, double eps);
 double orc_ghost_rule_fakhari(double phiF, double eps);
 

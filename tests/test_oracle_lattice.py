@@ -190,6 +190,35 @@ def test_post_collision_total_is_fixed(Q):
 
 
 @pytest.mark.parametrize("Q", [9, 19])
+def test_segregation_moves_color_up_its_gradient_and_conserves_it(Q):
+    """Eq. (segragationStepBlue) writes B*_i = phi N*_i plus a recoloring
+    term.  The term carries no color: sum_i B*_i = phi sum_i N*_i, the fact FP16
+    storage writes its rest populations from.  Inside the interface it sends
+    color along grad phi: B*_i - phi N*_i has the sign of c_i . grad phi.  It
+    vanishes in the pure phases (phi = 0, 1) and where grad phi = 0."""
+    rng = np.random.default_rng(19)
+    D = 2 if Q == 9 else 3
+    t = oracle.lattice_tables(Q, MPHI)
+    c = t["c"].astype(float)
+    for _ in range(50):
+        Nst = t["chi"] + rng.normal(0, 0.02, Q)
+        phi = rng.uniform(0.05, 0.95)
+        g = np.zeros(3)
+        g[:D] = rng.normal(0, 0.1, D)
+        p = rng.uniform(-5e-3, 5e-3)
+        B = oracle.segregate(Q, Nst, phi, g, p)
+        assert abs(B.sum() - phi * Nst.sum()) < 1e-14
+        rec, cg = B - phi * Nst, c @ g
+        assert rec[0] == 0.0
+        assert np.array_equal(np.sign(rec[1:]), np.sign(cg[1:]))
+    Nst = t["chi"] + rng.normal(0, 0.02, Q)
+    g = np.array([0.1, -0.05, 0.02 if D == 3 else 0.0])
+    for phi in (0.0, 1.0):
+        assert np.array_equal(oracle.segregate(Q, Nst, phi, g, 1e-3), phi * Nst)
+    assert np.array_equal(oracle.segregate(Q, Nst, 0.3, np.zeros(3), 1e-3), 0.3 * Nst)
+
+
+@pytest.mark.parametrize("Q", [9, 19])
 def test_collision_at_tau_one_is_bgk(Q):
     """At tau = 1 every rate is 1 and Eq. (MRTCOLL) reduces to N* = Neq + F_i / 2."""
     rng = np.random.default_rng(8)
