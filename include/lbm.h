@@ -15,9 +15,15 @@
  *   - device memory   owned by the library, or carved from a caller workspace
  *   - errors          no call aborts or throws; each returns an lbm_status and
  *                     lbm_last_error() gives a one-line message.  Device-side
- *                     failures (non-finite values) are latched on the device
- *                     and reported by the next synchronising call
- *                     (lbm_diagnostics, lbm_read_state, lbm_sync).
+ *                     failures (non-finite values, a halo copy that did not
+ *                     complete) are latched on the device and reported by the
+ *                     next synchronising call (lbm_diagnostics, lbm_sync,
+ *                     lbm_batch_sync).  After LBM_ERR_TIMEOUT the domain is
+ *                     poisoned: a tile of some step was skipped, so its state
+ *                     is wrong, and every later call that would change or
+ *                     advance it (lbm_step, lbm_init_*, lbm_write_state,
+ *                     lbm_profile_steps, lbm_batch_create/step/tune with it)
+ *                     returns LBM_ERR_TIMEOUT; destroy it and create another.
  *   - threads         one host thread per domain at a time
  */
 #ifndef LBM_H
@@ -38,8 +44,11 @@ typedef enum {
     LBM_ERR_OOM = -2,          /* device allocation failed or workspace too small */
     LBM_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     LBM_ERR_UNSTABLE = -4,     /* a step produced a non-finite velocity or color */
-    LBM_ERR_TIMEOUT = -5,      /* a bounded device wait gave up (a step kernel's TMA halo copy did not complete) */
-    LBM_ERR_UNSUPPORTED = -6   /* valid request the library does not implement */
+    LBM_ERR_TIMEOUT = -5,      /* a bounded device wait gave up (a step kernel's TMA halo copy did not
+                                  complete within 1 s or 2^22 polls); the domain is poisoned, see above */
+    LBM_ERR_UNSUPPORTED = -6,  /* valid request the library does not implement */
+    LBM_ERR_BOUNDS = -7        /* debug bounds-check library only (liblbm_debug.so): a kernel computed an
+                                  index outside its array; the access was skipped, the state is not valid */
 } lbm_status;
 
 typedef enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 } lbm_lattice;
@@ -150,8 +159,13 @@ size_t lbm_domain_bytes(const lbm_params* params, int64_t n_ghosts);
  * dev_workspace: NULL to let the library allocate, else a device pointer of
  * ws_bytes >= lbm_domain_bytes(...) that the caller keeps alive until
  * lbm_destroy.  cuda_stream: cudaStream_t every device call is issued on
- * (NULL = default stream).  Errors: LBM_ERR_ARG (parameters, mask or ghost
- * list), LBM_ERR_OOM, LBM_ERR_CUDA.  On error *out is NULL. */
+ * (NULL = default stream).  The step kernel copies each tile's color and
+ * velocity halo with tiled TMA copies where the tile needs no periodic image
+ * in y and z; with the environment variable LBM_HALO_COPY=elements set when
+ * the domain is created, every tile copies its halo element by element
+ * instead (same results; the reference the tiled copies are tested
+ * against).  Errors: LBM_ERR_ARG (parameters, mask or ghost list),
+ * LBM_ERR_OOM, LBM_ERR_CUDA.  On error *out is NULL. */
 lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid,
                              const lbm_ghost* ghosts, int64_t n_ghosts,
                              void* dev_workspace, size_t ws_bytes,
@@ -224,13 +238,18 @@ int64_t lbm_fluid_nodes(const lbm_domain* dom);
  *   dev_u      T[n_components][plane] velocity components (may be NULL if
  *              n_components = 0), plane >= n_nodes
  *   dev_out    double[6], written: fluid node count, sum phi, rho_l sum phi,
- *              rho_g sum (1-phi), max |u|, count of non-finite phi or u
+ *              rho_g sum (1-phi), max |u| over the nodes where |u|^2 is
+ *              finite, count of fluid nodes whose phi or |u|^2 is NaN or
+ *              infinite (the sums include such values as they are)
  * Everything is device memory owned by the caller; the call only enqueues two
  * kernels on cuda_stream (NULL = default stream) and returns.  It allocates
  * nothing: its scratch is a static 64 KiB array inside the library that each
  * GPU loading the library keeps until the process exits.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call outside any stream capture.  All calls on a
+ * caches it; make that first call outside any stream capture.  The cached
+ * address belongs to the device's primary context: after cudaDeviceReset
+ * (or any reset of that context) the library reloads and the array may
+ * move, so do not call this entry point again in that process.  All calls on a
  * GPU share the array, so calls whose kernels overlap on the GPU (different
  * streams, no ordering between them) race and give wrong sums; calls on one
  * stream are safe.  n_nodes above 16,777,216 (the array's capacity of 1024
@@ -240,6 +259,40 @@ lbm_status lbm_phase_sums_noalloc(const uint8_t* dev_class, const void* dev_phi,
                                   int32_t precision, int32_t n_components, int64_t n_nodes,
                                   int64_t plane, double rho_l, double rho_g, double* dev_out,
                                   void* cuda_stream, char* err, size_t err_len);
+
+/* Fault-path check of the bounded halo-copy wait (no counterpart in the
+ * paper: a service of this library for testing its error reporting).  The
+ * step kernel waits for each tile's TMA halo copy on a shared-memory mbarrier
+ * with a bounded wait; if that wait gives up, the kernel sets the domain's
+ * timeout bit instead of hanging.  A copy that never lands cannot be made
+ * without faulting the GPU, so this call enqueues on the domain stream one
+ * block that arms an mbarrier for 4096 bytes no copy will deliver (no TMA or
+ * bulk copy is issued at all), waits on it with the step kernel's own wait
+ * function and a limit of timeout_ns (1e3 .. 1e9 ns), sets the same timeout
+ * bit and exits with nothing in flight.  The next synchronising call then
+ * returns LBM_ERR_TIMEOUT and the domain is poisoned exactly as after a real
+ * timeout.  waited_ns (may be NULL) receives the block's measured wait, which
+ * makes the call synchronise the stream (it then also allocates and frees 8
+ * bytes of device memory with cudaMallocAsync/cudaFreeAsync).  Errors:
+ * LBM_ERR_ARG (timeout_ns out of range), LBM_ERR_TIMEOUT (already
+ * poisoned), LBM_ERR_CUDA, LBM_ERR_OOM. */
+lbm_status lbm_debug_expire_halo_wait(lbm_domain* dom, int64_t timeout_ns, int64_t* waited_ns);
+
+/* The bounds-checked build of this library (liblbm_debug.so, the same sources
+ * compiled with LBM_DEBUG_BOUNDS; no counterpart in the paper) tests every
+ * index its kernels compute against the array it addresses -- streaming pull
+ * sources, bounce-back slots, halo slots, ghost corners and nodes, tiled-copy
+ * boxes, batch tiles -- before the access.  A bad index sets a bit that the
+ * next synchronising call reports as LBM_ERR_BOUNDS, and the access is
+ * skipped (a load reads element 0, a store is dropped); nothing traps.
+ * lbm_debug_bounds_checked returns 1 in that build and 0 in the production
+ * library.  lbm_debug_plant_bad_index(dom, 0) points the first corner of the
+ * domain's first ghost past the end of the color array, so that the next
+ * step's ghost update meets an index its check must catch; it synchronises,
+ * and in the production library it returns LBM_ERR_UNSUPPORTED and writes
+ * nothing.  Errors: LBM_ERR_ARG (which != 0, no ghost nodes), LBM_ERR_CUDA. */
+int32_t lbm_debug_bounds_checked(void);
+lbm_status lbm_debug_plant_bad_index(lbm_domain* dom, int32_t which);
 
 /* ---- Batches: several domains advanced together (no counterpart in the
  * paper, which runs one case at a time).  A batch advances domains of the same

@@ -3,6 +3,7 @@
 // step replay, state transfer and diagnostics.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -13,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm.h"
+#include "lbm_domain_access.h"
 #include "lbm_launch.cuh"
 
 using namespace lbmgpu;
@@ -114,6 +116,11 @@ struct lbm_domain {
     // halo copies (FP32 arithmetic, rows of a multiple of 16 bytes)
     bool tma = false;
     CUtensorMap tm_phi{}, tm_u[2]{};
+    bool tma2 = false;                     // the same with the two-node kernel's box
+    CUtensorMap tm2_phi{}, tm2_u[2]{};
+    // set once a bounded halo-copy wait gave up (LBM_ERR_TIMEOUT): a skipped
+    // tile left the state wrong, so the domain takes no further steps
+    bool poisoned = false;
 
     template <typename P> P* at(size_t off) const { return reinterpret_cast<P*>(ws + off); }
     void* N(int k) const { return at<void>(lay.off_N[k]); }
@@ -140,6 +147,19 @@ lbm_status fail(lbm_domain* d, lbm_status s, const std::string& msg) {
     if (d) d->err = msg; else g_create_error = msg;
     return s;
 }
+}  // namespace
+
+namespace lbmgpu {
+int* domain_error_flag(lbm_domain* d) { return d->errflag(); }
+cudaStream_t domain_stream(lbm_domain* d) { return d->stream; }
+bool domain_poisoned(const lbm_domain* d) { return d->poisoned; }
+int32_t* domain_ghost_corners(lbm_domain* d) { return d->at<int32_t>(d->lay.off_gcorner); }
+int64_t domain_ghosts(const lbm_domain* d) { return d->ng; }
+int64_t domain_plane(const lbm_domain* d) { return d->lay.plane; }
+lbm_status domain_fail(lbm_domain* d, lbm_status s, const char* msg) { return fail(d, s, msg); }
+}  // namespace lbmgpu
+
+namespace {
 
 #define CUDA_TRY(dom, call)                                                                        \
     do {                                                                                           \
@@ -229,9 +249,9 @@ lbm_status prepare_ghosts(lbm_domain* d, const lbm_ghost* ghosts) {
             double wk = 1.0;
             for (int a = 0; a < D; ++a) {
                 const int bit = (k >> a) & 1;
-                int64_t v = (int64_t)base[a] + bit;
-                v %= dims[a];
-                if (v < 0) v += dims[a];
+                int64_t v = (int64_t)base[a] + bit;       // within one cell of the ghost: x - 1 .. x + 2
+                while (v < 0) v += dims[a];
+                while (v >= dims[a]) v -= dims[a];
                 c[a] = v;
                 wk *= bit ? frac[a] : 1.0 - frac[a];
             }
@@ -280,7 +300,8 @@ void launch_one_step(lbm_domain* d, int cur, cudaStream_t s, cudaEvent_t* ev = n
         const void* wt = d->at<void>(L.off_gwt);
         dispatch(d, [&](auto Lx) {
             decltype(Lx)::ghost(L.GK, d->cfg.ghost_rule, d->ng, d->at<int32_t>(L.off_gnode),
-                                d->at<int32_t>(L.off_gcorner), wt, d->cfg.exp_eps, d->cfg.eps, d->phi(), s);
+                                d->at<int32_t>(L.off_gcorner), wt, d->cfg.exp_eps, d->cfg.eps, d->phi(), L.plane,
+                                d->errflag(), s);
         });
     }
     StepPtrs sp;
@@ -288,10 +309,11 @@ void launch_one_step(lbm_domain* d, int cur, cudaStream_t s, cudaEvent_t* ev = n
     sp.phi = d->phi(); sp.u_in = d->U(cur); sp.u_out = d->U(1 - cur); sp.p = d->p();
     sp.mask = d->mask(); sp.err = d->errflag();
     if (d->tma) { sp.tm_phi = &d->tm_phi; sp.tm_u = &d->tm_u[cur]; }
+    if (d->tma2) { sp.tm2_phi = &d->tm2_phi; sp.tm2_u = &d->tm2_u[cur]; }
     if (ev) cudaEventRecord(ev[1], s);
     dispatch(d, [&](auto Lx) { decltype(Lx)::step(d->cfg, sp, s); });
     if (ev) cudaEventRecord(ev[2], s);
-    dispatch(d, [&](auto Lx) { decltype(Lx)::phi(d->cfg, d->B(1 - cur), d->mask(), d->phi(), s); });
+    dispatch(d, [&](auto Lx) { decltype(Lx)::phi(d->cfg, d->B(1 - cur), d->mask(), d->phi(), d->errflag(), s); });
     if (ev) cudaEventRecord(ev[3], s);
 }
 
@@ -327,12 +349,12 @@ EncodeTiledFn encode_tiled() {
 
 // Tensor maps for the halo copies of the step kernel: phi as (nx, ny, nz) and
 // each velocity buffer as (nx, ny, nz, D) floats, box = the halo tile of
-// Tile<Q>.  Only for float fields whose rows are a multiple of 16 bytes (the
-// strides TMA accepts); otherwise, or if the driver refuses, the kernel copies
-// every halo element itself.
-template <int Q>
-bool make_halo_maps(lbm_domain* d) {
-    using Tl = Tile<Q>;
+// Tile<Q, V>; out[0] = phi, out[1 + k] = velocity buffer k.  Only for float
+// fields whose rows are a multiple of 16 bytes (the strides TMA accepts);
+// otherwise, or if the driver refuses, the kernel copies every halo element
+// itself.
+template <class Tl>
+bool encode_halo_maps_tile(const lbm_domain* d, CUtensorMap out[3]) {
     const lbm_params& P = d->prm;
     if (d->fp64) return false;
     EncodeTiledFn enc = encode_tiled();
@@ -348,14 +370,67 @@ bool make_halo_maps(lbm_domain* d) {
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
-    return one(&d->tm_phi, d->phi(), 3) && one(&d->tm_u[0], d->U(0), 4) && one(&d->tm_u[1], d->U(1), 4);
+    return one(&out[0], d->phi(), 3) && one(&out[1], d->U(0), 4) && one(&out[2], d->U(1), 4);
 }
+
+template <int Q, int V>
+bool encode_halo_maps(const lbm_domain* d, CUtensorMap out[3]) {
+    return encode_halo_maps_tile<Tile<Q, V>>(d, out);
+}
+
+template <int Q>
+bool make_pair_maps(lbm_domain* d) {
+    CUtensorMap m[3];
+    if (!encode_halo_maps_tile<PairTile<Q>>(d, m)) return false;
+    d->tm2_phi = m[0];
+    d->tm2_u[0] = m[1];
+    d->tm2_u[1] = m[2];
+    return true;
+}
+
+template <int Q>
+bool make_halo_maps(lbm_domain* d) {
+    CUtensorMap m[3];
+    if (!encode_halo_maps<Q, 0>(d, m)) return false;
+    d->tm_phi = m[0];
+    d->tm_u[0] = m[1];
+    d->tm_u[1] = m[2];
+    return true;
+}
+
+// The maps of tile shape V for a domain of lattice Q (the batch's tables).
+bool encode_halo_maps_any(const lbm_domain* d, int V, CUtensorMap out[3]) {
+    if (d->prm.lattice == 9) {
+        switch (V) {
+        case 0: return encode_halo_maps<9, 0>(d, out);
+        case 1: return encode_halo_maps<9, 1>(d, out);
+        case 2: return encode_halo_maps<9, 2>(d, out);
+        case 3: return encode_halo_maps<9, 3>(d, out);
+        default: return encode_halo_maps<9, 4>(d, out);
+        }
+    }
+    switch (V) {
+    case 0: return encode_halo_maps<19, 0>(d, out);
+    case 1: return encode_halo_maps<19, 1>(d, out);
+    case 2: return encode_halo_maps<19, 2>(d, out);
+    case 3: return encode_halo_maps<19, 3>(d, out);
+    default: return encode_halo_maps<19, 4>(d, out);
+    }
+}
+
+const char* const kPoisonedMsg =
+    "a bounded halo-copy wait gave up earlier (LBM_ERR_TIMEOUT); the domain's state is not valid: destroy it";
 
 lbm_status check_err_flag(lbm_domain* d) {
     int h = 0;
     CUDA_TRY(d, cudaMemcpyAsync(&h, d->errflag(), sizeof(int), cudaMemcpyDeviceToHost, d->stream));
     CUDA_TRY(d, cudaStreamSynchronize(d->stream));
-    if (h & kErrCopyTimeout) return fail(d, LBM_ERR_TIMEOUT, "a halo copy of the step kernel did not complete");
+    if (h & kErrCopyTimeout) {
+        d->poisoned = true;
+        return fail(d, LBM_ERR_TIMEOUT, "a halo copy of the step kernel did not complete");
+    }
+    if (h & kErrBounds)
+        return fail(d, LBM_ERR_BOUNDS, "a step kernel computed an index outside its array (access skipped)");
     if (h) return fail(d, LBM_ERR_UNSTABLE, "a step produced a non-finite velocity");
     return LBM_OK;
 }
@@ -498,6 +573,10 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     c.eps = -(4.0 / P.W) * std::cos(P.theta);
     c.exp_eps = std::exp(c.eps);
     c.ghost_rule = P.ghost_rule;
+    // float arithmetic: the one-node step kernel, or the two-node kernel with
+    // LBM_STEP_KERNEL=pair (both give the same results to the bit)
+    const char* step_kernel = std::getenv("LBM_STEP_KERNEL");
+    c.pair = P.precision != LBM_FP64 && step_kernel && std::strcmp(step_kernel, "pair") == 0;
 
     // node classes: a solid node with a fluid stencil neighbour is a ghost
     const int64_t nn = L.nn_dense;
@@ -505,20 +584,34 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     d->h_cls.assign(nn, CLS_FLUID);
     std::vector<int> ox, oy, oz;
     stencil_offsets(P.lattice, ox, oy, oz);
-    int64_t n_cls_ghost = 0;
+    int64_t n_cls_ghost = 0, n_solid = 0;
+    uint8_t* cls_out = d->h_cls.data();
     for (int64_t z = 0; z < nz; ++z)
-        for (int64_t y = 0; y < ny; ++y)
+        for (int64_t y = 0; y < ny; ++y) {
+            const uint8_t* row = solid + nx * (y + ny * z);
             for (int64_t x = 0; x < nx; ++x) {
-                const int64_t node = x + nx * (y + ny * z);
-                if (!solid[node]) { d->n_fluid++; continue; }
+                if (!row[x]) {                          // fluid: the class array starts as all fluid
+                    if ((x & 7) == 0 && x + 8 <= nx) {  // skip eight fluid nodes at a time
+                        uint64_t w;
+                        std::memcpy(&w, row + x, 8);
+                        if (w == 0) x += 7;
+                    }
+                    continue;
+                }
+                ++n_solid;
                 uint8_t cl = CLS_SOLID;
                 for (size_t j = 0; j < ox.size(); ++j) {
-                    const int64_t xx = (x + ox[j] + nx) % nx, yy = (y + oy[j] + ny) % ny, zz = (z + oz[j] + nz) % nz;
+                    int64_t xx = x + ox[j], yy = y + oy[j], zz = z + oz[j];
+                    xx += xx < 0 ? nx : (xx >= nx ? -nx : 0);
+                    yy += yy < 0 ? ny : (yy >= ny ? -ny : 0);
+                    zz += zz < 0 ? nz : (zz >= nz ? -nz : 0);
                     if (!solid[xx + nx * (yy + ny * zz)]) { cl = CLS_GHOST; break; }
                 }
-                d->h_cls[node] = cl;
+                cls_out[x + nx * (y + ny * z)] = cl;
                 n_cls_ghost += cl == CLS_GHOST;
             }
+        }
+    d->n_fluid = nn - n_solid;
     const int64_t ext[3] = {nx, ny, nz};
     for (int a = 0; a < L.D; ++a) {
         if (P.periodic & (1u << a)) continue;
@@ -565,14 +658,20 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
         return fail(nullptr, LBM_ERR_CUDA, msg);
     };
     if (cudaStreamCreateWithFlags(&d->cap, cudaStreamNonBlocking) != cudaSuccess) return bail("cudaStreamCreate failed");
-    d->tma = P.lattice == 9 ? make_halo_maps<9>(d) : make_halo_maps<19>(d);
+    // LBM_HALO_COPY=elements: every tile copies its halo element by element
+    // (the reference the tiled copies are tested against)
+    const char* halo_copy = std::getenv("LBM_HALO_COPY");
+    const bool elements_only = halo_copy && std::strcmp(halo_copy, "elements") == 0;
+    d->tma = !elements_only && (P.lattice == 9 ? make_halo_maps<9>(d) : make_halo_maps<19>(d));
+    d->tma2 = !elements_only && (P.lattice == 9 ? make_pair_maps<9>(d) : make_pair_maps<19>(d));
     // upload node classes and the ghost table; the bounce-back mask is built on the device
     // device node indices use the padded row pitch
     std::vector<int32_t> gnode(n_ghosts), pcorner(d->h_corner.size());
     for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)padded_node(d, ghosts[g].node);
     for (size_t k = 0; k < pcorner.size(); ++k) pcorner[k] = (int32_t)padded_node(d, d->h_corner[k]);
     std::vector<uint8_t> pcls((size_t)L.nn, CLS_SOLID);
-    for (int64_t k = 0; k < nn; ++k) pcls[padded_node(d, k)] = d->h_cls[k];
+    for (int64_t r = 0; r < nn / nx; ++r)                  // row by row: the padding columns stay solid
+        std::memcpy(&pcls[(size_t)(r * L.px)], &d->h_cls[(size_t)(r * nx)], (size_t)nx);
     cudaStream_t s = d->stream;
     if (cudaMemsetAsync(d->ws, 0, L.total, s) != cudaSuccess) return bail("cudaMemset failed");
     if (cudaMemcpyAsync(d->cls(), pcls.data(), L.nn, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -602,6 +701,7 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
 
 lbm_status lbm_init_droplet(lbm_domain* d, const double centre[3], double R0) {
     if (!d || !centre) return fail(d, LBM_ERR_ARG, "NULL argument");
+    if (d->poisoned) return fail(d, LBM_ERR_TIMEOUT, kPoisonedMsg);
     if (!(R0 > 0) || !std::isfinite(centre[0]) || !std::isfinite(centre[1]) || !std::isfinite(centre[2]))
         return fail(d, LBM_ERR_ARG, "drop radius must be positive and the centre finite");
     return init_state(d, 0, centre, R0);
@@ -609,6 +709,7 @@ lbm_status lbm_init_droplet(lbm_domain* d, const double centre[3], double R0) {
 
 lbm_status lbm_init_phi(lbm_domain* d, const double* phi_host) {
     if (!d || !phi_host) return fail(d, LBM_ERR_ARG, "NULL argument");
+    if (d->poisoned) return fail(d, LBM_ERR_TIMEOUT, kPoisonedMsg);
     lbm_status st = upload(d, d->phi(), phi_host, d->lay.nn_dense);
     if (st != LBM_OK) return st;
     const double zero[3] = {0, 0, 0};
@@ -618,6 +719,7 @@ lbm_status lbm_init_phi(lbm_domain* d, const double* phi_host) {
 lbm_status lbm_step(lbm_domain* d, int64_t n) {
     if (!d) return fail(d, LBM_ERR_ARG, "NULL domain");
     if (n < 0) return fail(d, LBM_ERR_ARG, "n must be >= 0");
+    if (d->poisoned) return fail(d, LBM_ERR_TIMEOUT, kPoisonedMsg);
     while (n > 0) {
         if (d->cur == 0 && n >= GRAPH_STEPS) {
             CUDA_TRY(d, cudaGraphLaunch(d->g8, d->stream));
@@ -636,6 +738,7 @@ lbm_status lbm_step(lbm_domain* d, int64_t n) {
 lbm_status lbm_profile_steps(lbm_domain* d, int64_t n, double kernel_ms[3]) {
     if (!d || !kernel_ms) return fail(d, LBM_ERR_ARG, "NULL argument");
     if (n < 1) return fail(d, LBM_ERR_ARG, "n must be >= 1");
+    if (d->poisoned) return fail(d, LBM_ERR_TIMEOUT, kPoisonedMsg);
     cudaEvent_t ev[4];
     for (int k = 0; k < 4; ++k) CUDA_TRY(d, cudaEventCreate(&ev[k]));
     lbm_status st = LBM_OK;
@@ -745,10 +848,18 @@ lbm_status lbm_read_state(lbm_domain* d, int32_t field, double* host_out) {
         void* st = is_b ? d->B(d->cur) : d->N(d->cur);
         void* stage = d->at<void>(L.off_stage);
         for (int i = 0; i < L.Q; ++i) {
-            dispatch(d, [&](auto Lx) { decltype(Lx)::gather_dir(d->cfg, d->cls(), i, is_b, st, stage, d->stream); });
+            double base = 0.0;
+            dispatch(d, [&](auto Lx) {
+                decltype(Lx)::gather_dir(d->cfg, d->cls(), i, is_b, st, stage, d->stream);
+                base = decltype(Lx)::storage_base(d->cfg, i, is_b);
+            });
             CUDA_TRY(d, cudaGetLastError());
-            lbm_status s = download(d, host_out + (size_t)i * nn, stage, nn);
+            double* out = host_out + (size_t)i * nn;
+            lbm_status s = download(d, out, stage, nn);
             if (s != LBM_OK) return s;
+            if (base != 0.0)                       // deviations from the storage reference -> values, in double
+                for (int64_t k = 0; k < nn; ++k)
+                    if (d->h_cls[k] == CLS_FLUID) out[k] += base;
         }
         return LBM_OK;
     }
@@ -773,6 +884,7 @@ lbm_status lbm_read_state(lbm_domain* d, int32_t field, double* host_out) {
 
 lbm_status lbm_write_state(lbm_domain* d, int32_t field, const double* host_in) {
     if (!d || !host_in) return fail(d, LBM_ERR_ARG, "NULL argument");
+    if (d->poisoned) return fail(d, LBM_ERR_TIMEOUT, kPoisonedMsg);
     const Layout& L = d->lay;
     const int64_t nn = L.nn_dense;
     switch (field) {
@@ -781,10 +893,18 @@ lbm_status lbm_write_state(lbm_domain* d, int32_t field, const double* host_in) 
         const bool is_b = field == LBM_FIELD_B;
         void* st = is_b ? d->B(d->cur) : d->N(d->cur);
         char* stage = d->at<char>(L.off_stage);
+        std::vector<double> dev_i((size_t)nn), dev_o((size_t)nn);
         for (int i = 0; i < L.Q; ++i) {
             const int o = d->prm.lattice == 9 ? Lattice<9>::opp(i) : Lattice<19>::opp(i);
-            lbm_status s = upload(d, stage, host_in + (size_t)i * nn, nn);
-            if (s == LBM_OK) s = upload(d, stage + (size_t)L.plane * L.elem, host_in + (size_t)o * nn, nn);
+            double base = 0.0;                     // the same for i and its opposite (chi is even in c)
+            dispatch(d, [&](auto Lx) { base = decltype(Lx)::storage_base(d->cfg, i, is_b); });
+            // values -> deviations from the storage reference, in double
+            for (int64_t k = 0; k < nn; ++k) {
+                dev_i[k] = host_in[(size_t)i * nn + k] - base;
+                dev_o[k] = host_in[(size_t)o * nn + k] - base;
+            }
+            lbm_status s = upload(d, stage, dev_i.data(), nn);
+            if (s == LBM_OK) s = upload(d, stage + (size_t)L.plane * L.elem, dev_o.data(), nn);
             if (s != LBM_OK) return s;
             dispatch(d, [&](auto Lx) {
                 decltype(Lx)::scatter_dir(d->cfg, d->cls(), i, is_b, stage, stage + (size_t)L.plane * L.elem, st,
@@ -873,7 +993,7 @@ struct lbm_batch {
     std::vector<int> slots;            // each domain's slot of the constant table
     char* dev = nullptr;               // one allocation for every device table
     int4* tiles[kTileVariants] = {};             // {slot, x0, y0, z0}
-    CUtensorMap* maps = nullptr;                 // [kBatchSlots][3] halo maps by slot (see k_step_batched)
+    CUtensorMap* maps = nullptr;                 // [kTileVariants][kBatchSlots][3] halo maps by shape and slot
     void* ghost_tabs = nullptr;
     int64_t* ghost_begin = nullptr;
     int64_t total_ghosts = 0;
@@ -939,7 +1059,8 @@ void batch_launch_step(lbm_batch* b, int parity, cudaStream_t s) {
     bdispatch(b->precision, [&](auto Lx) {
         using L = decltype(Lx);
         L::ghost_batched(b->GK, b->ghost_tabs, b->ghost_begin, (int)b->doms.size(), b->total_ghosts, s);
-        L::step_phi_batched(b->Q, V, b->tiles[V], b->maps, b->ntiles[V], b->ncontrast[V], parity, s);
+        L::step_phi_batched(b->Q, V, b->tiles[V], b->maps + (size_t)V * kBatchSlots * 3, b->ntiles[V],
+                            b->ncontrast[V], parity, s);
     });
 }
 
@@ -988,6 +1109,10 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
         }
         for (int j = 0; j < i; ++j)
             if (doms[j] == doms[i]) { delete b; return bfail(nullptr, LBM_ERR_ARG, "a domain appears twice"); }
+        if (doms[i]->poisoned) {
+            delete b;
+            return bfail(nullptr, LBM_ERR_TIMEOUT, "domain " + std::to_string(i) + ": " + kPoisonedMsg);
+        }
         b->doms.push_back(doms[i]);
         b->cur0.push_back(doms[i]->cur);
     }
@@ -1009,6 +1134,25 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
         using L = decltype(Lx);
         esz = L::entry_size(); gsz = L::ghost_table_size();
     });
+    // halo maps by tile shape and slot: phi, then u_in of step parity 0 and 1
+    // (u_in = U(cur0 ^ parity)), each with the box of that shape's halo tile
+    std::vector<CUtensorMap> hm((size_t)kTileVariants * kBatchSlots * 3);
+    std::vector<char> slot_tma(kBatchSlots, 0);
+    for (int i = 0; i < n; ++i) {
+        lbm_domain* d = b->doms[i];
+        if (!d->tma) continue;
+        const int sl = b->slots[i];
+        bool ok = true;
+        for (int V = 0; V < kTileVariants && ok; ++V) {
+            CUtensorMap m[3];
+            ok = encode_halo_maps_any(d, V, m);
+            CUtensorMap* dst = &hm[((size_t)V * kBatchSlots + sl) * 3];
+            dst[0] = m[0];
+            dst[1] = m[1 + b->cur0[i]];
+            dst[2] = m[1 + (b->cur0[i] ^ 1)];
+        }
+        slot_tma[sl] = ok;                       // a slot uses its maps only if every shape's encoded
+    }
     std::vector<char> he(esz * n), hg(gsz * n);
     std::vector<int64_t> gbegin(n + 1, 0);
     std::vector<std::vector<int4>> tiles(kTileVariants);
@@ -1024,9 +1168,10 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
                 sp[k].phi = d->phi(); sp[k].u_in = d->U(c); sp[k].u_out = d->U(1 - c); sp[k].p = d->p();
                 sp[k].mask = d->mask(); sp[k].err = d->errflag();
             }
-            LL::fill_entry(&he[esz * i], d->cfg, sp, d->tma);
+            LL::fill_entry(&he[esz * i], d->cfg, sp, slot_tma[b->slots[i]] != 0);
             LL::fill_ghost_table(&hg[gsz * i], d->ng, d->at<int32_t>(L.off_gnode), d->at<int32_t>(L.off_gcorner),
-                                 d->at<void>(L.off_gwt), d->cfg.exp_eps, d->cfg.eps, d->phi(), d->cfg.ghost_rule);
+                                 d->at<void>(L.off_gwt), d->cfg.exp_eps, d->cfg.eps, d->phi(), d->cfg.ghost_rule,
+                                 L.plane, d->errflag());
         });
         gbegin[i + 1] = gbegin[i] + d->ng;
     }
@@ -1043,16 +1188,6 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t r = off; off = round_up(off + bytes, 256); return r; };
     const size_t o_g = take(hg.size()), o_gb = take(gbegin.size() * 8);
-    // halo maps by slot: phi, then u_in of step parity 0 and 1 (u_in = U(cur0 ^ parity))
-    std::vector<CUtensorMap> hm((size_t)kBatchSlots * 3);
-    for (int i = 0; i < n; ++i) {
-        lbm_domain* d = b->doms[i];
-        if (!d->tma) continue;
-        const int sl = b->slots[i];
-        hm[3 * sl] = d->tm_phi;
-        hm[3 * sl + 1] = d->tm_u[b->cur0[i]];
-        hm[3 * sl + 2] = d->tm_u[b->cur0[i] ^ 1];
-    }
     const size_t o_m = take(hm.size() * sizeof(CUtensorMap));
     size_t o_t[kTileVariants];
     for (int V = 0; V < kTileVariants; ++V) {
@@ -1099,9 +1234,12 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
 lbm_status lbm_batch_step(lbm_batch* b, int64_t n) {
     if (!b) return bfail(b, LBM_ERR_ARG, "NULL batch");
     if (n < 0) return bfail(b, LBM_ERR_ARG, "n must be >= 0");
-    for (size_t i = 0; i < b->doms.size(); ++i)
+    for (size_t i = 0; i < b->doms.size(); ++i) {
         if (b->doms[i]->cur != (b->cur0[i] ^ b->parity))
             return bfail(b, LBM_ERR_ARG, "domain " + std::to_string(i) + " was stepped outside the batch; recreate it");
+        if (b->doms[i]->poisoned)
+            return bfail(b, LBM_ERR_TIMEOUT, "domain " + std::to_string(i) + ": " + kPoisonedMsg);
+    }
     int64_t left = n;
     while (left > 0) {
         cudaError_t e;
@@ -1129,6 +1267,9 @@ lbm_status lbm_batch_sync(lbm_batch* b) {
 
 lbm_status lbm_batch_tune(lbm_batch* b, int32_t steps_per_trial, int32_t* chosen, double* ms_per_step) {
     if (!b || steps_per_trial < 1) return bfail(b, LBM_ERR_ARG, "bad arguments");
+    for (size_t i = 0; i < b->doms.size(); ++i)
+        if (b->doms[i]->poisoned)
+            return bfail(b, LBM_ERR_TIMEOUT, "domain " + std::to_string(i) + ": " + kPoisonedMsg);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, LBM_ERR_CUDA, "cudaEventCreate failed");

@@ -106,8 +106,12 @@ __global__ void k_init_pops(Dims d, StepParams<T> P, const uint8_t* __restrict__
             const int64_t dn = shifted(d, x, y, z, L::cx(i), L::cy(i), L::cz(i));
             const T ph = (cls[dn] == CLS_FLUID) ? phi[dn] : phi[node];
             const int pl = (int)d.plane, nd = (int)node;
-            pop_store<S, T>(Nst, i, pl, nd, kShift ? T(0) : P.chi[i], kScaleN);
-            pop_store<S, T>(Bst, i, pl, nd, kShift ? (ph - T(0.5)) * P.chi[i] : ph * P.chi[i], kScaleB);
+            // deviation storage: N_i - chi_i(stored) = the exact chi_i minus the
+            // stored one; B_i - chi_i(stored)/2 = phi (that) + (phi - 1/2) chi_i(stored)
+            const T e = P.chi_err[i == 0 ? 0 : (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i) == 1
+                                                    ? 1 : 2)];
+            pop_store<S, T>(Nst, i, pl, nd, kShift ? e : P.chi[i], kScaleN);
+            pop_store<S, T>(Bst, i, pl, nd, kShift ? (ph - T(0.5)) * P.chi[i] + ph * e : ph * P.chi[i], kScaleB);
         }
     }
 }
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rh
             u2 += ua * ua;
         }
         if (u2 > acc[DG_MAXU2]) acc[DG_MAXU2] = u2;
-        if (!(u2 == u2) || !(ph == ph)) acc[DG_NAN] += 1.0;
+        if (!isfinite(u2) || !isfinite(ph)) acc[DG_NAN] += 1.0;     // NaN or +-Inf in phi or u
         const double phh = (rho_l * ph + rho_g * (1.0 - ph)) * (double)p[node];
         if (ph > 1.0 - 1e-3) { acc[DG_PIN] += phh; acc[DG_NIN] += 1.0; }
         if (ph < 1e-3) { acc[DG_POUT] += phh; acc[DG_NOUT] += 1.0; }

@@ -49,7 +49,11 @@ struct StepParams {
     T nu_l, nu_g;            // kinematic viscosities
     T k48W, k3W2, two_over_W;   // 48/W, 3W/2, 2/W
     T g[3];
-    T chi[19];
+    T chi[19];               // float arithmetic: the storage reference, on a 2^-24 grid, summing to exactly 1
+    // chi_i - (the chi[i] above) by direction class (0 rest, 1 axis, 2
+    // diagonal/edge): zero in FP64; in float arithmetic the equilibrium and the
+    // pressure's zero are taken at the exact chi through these corrections
+    T chi_err[3];
     T c2chi;                 // sum_i chi_i c_ix^2 = (1-alpha) c_s^2/(1-w_0)
     T exp_eps;               // exp(eps), eps = -(4/W) cos(theta)
 };
@@ -102,6 +106,13 @@ template <> struct PopStore<double> : PlainStore<double> {
 };
 template <> struct PopStore<float> : PlainStore<float> {
     static constexpr bool kShift = true, kExact = true;
+    // two adjacent nodes (idx even, so 8-byte aligned): values in storage units
+    __device__ static float2 load_units2(const float* m, int idx) {
+        return __ldg(reinterpret_cast<const float2*>(m + idx));
+    }
+    __device__ static void store_units2(float* m, int idx, float va, float vb, float&, float&) {
+        *reinterpret_cast<float2*>(m + idx) = make_float2(va, vb);
+    }
 };
 template <> struct PopStore<__half> {
     static constexpr bool kShift = true, kExact = false;     // moving populations are rounded on store
@@ -127,6 +138,17 @@ template <> struct PopStore<__half> {
         const __half h = __float2half_rn(v);
         m[idx] = h;
         acc = add_f16_f32(h, acc);
+    }
+    // two adjacent nodes (idx even, so 4-byte aligned): one 32-bit load or
+    // store for both, each value rounded as store_units rounds it
+    __device__ static float2 load_units2(const __half* m, int idx) {
+        return __half22float2(__ldg(reinterpret_cast<const __half2*>(m + idx)));
+    }
+    __device__ static void store_units2(__half* m, int idx, float va, float vb, float& accA, float& accB) {
+        const __half2 h = __floats2half2_rn(va, vb);
+        *reinterpret_cast<__half2*>(m + idx) = h;
+        accA = add_f16_f32(__low2half(h), accA);
+        accB = add_f16_f32(__high2half(h), accB);
     }
 };
 
@@ -189,6 +211,7 @@ struct Tile {
     static constexpr int HY = TY + 2;
     static constexpr int HZ = (D == 2) ? 1 : TZ + 2;
     static constexpr int HN = HX * HY * HZ;
+    static constexpr int BX = TX;              // threads along x: one node each
     static constexpr int THREADS = TX * TY * TZ;
     // offset of the halo slot of x + c in a halo tile
     __host__ __device__ static constexpr int off(int cx, int cy, int cz) { return cx + HX * (cy + HY * cz); }
@@ -266,10 +289,20 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
         "%5}], [%6];\n" ::"r"(smem_addr(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
         : "memory");
 }
-// Waits for phase `parity` of the barrier; false if it has not completed after
-// kMbarSpins polls (the caller then flags an error instead of waiting on).
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for phase `parity` of the barrier; false once timeout_ns have passed
+// since the first unsuccessful poll, or after kMbarSpins polls, whichever
+// comes first (the caller then flags an error instead of waiting on).  A
+// copy that has landed is seen at the first poll, without reading the timer.
 constexpr int kMbarSpins = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+constexpr uint64_t kMbarTimeoutNs = 1000000000ull;     // 1 s: a halo copy takes microseconds
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, uint64_t timeout_ns = kMbarTimeoutNs) {
+    uint64_t t0 = 0;
     for (int k = 0; k < kMbarSpins; ++k) {
         unsigned done;
         asm volatile(
@@ -278,24 +311,53 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
             : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((k & 15) == 0) {
+            const uint64_t t = globaltimer_ns();
+            if (k == 0) t0 = t;
+            else if (t - t0 >= timeout_ns) return false;
+        }
     }
     return false;
 }
-// error flag bits: 1 = non-finite value, 2 = a halo copy did not complete
-constexpr int kErrNonFinite = 1, kErrCopyTimeout = 2;
+// error flag bits: 1 = non-finite value, 2 = a halo copy did not complete,
+// 4 = an index out of range (debug bounds-check builds only)
+constexpr int kErrNonFinite = 1, kErrCopyTimeout = 2, kErrBounds = 4;
+
+// ---- debug bounds checks.  Built with LBM_DEBUG_BOUNDS, every index the step
+// kernels compute for a device access is tested against its array first: a
+// bad index sets kErrBounds in the domain's error word (the host reports
+// LBM_ERR_BOUNDS) and the access is skipped -- a load reads element 0
+// instead, a store is dropped.  Nothing traps.  Without the flag the tests
+// are constant true and compile away.
+#ifdef LBM_DEBUG_BOUNDS
+constexpr bool kDebugBounds = true;
+#else
+constexpr bool kDebugBounds = false;
+#endif
+__device__ __forceinline__ bool idx_ok(long long idx, long long n, int* err) {
+    if (kDebugBounds && (idx < 0 || idx >= n)) {
+        if (err) atomicOr(err, kErrBounds);
+        return false;
+    }
+    return true;
+}
+template <typename I>
+__device__ __forceinline__ I idx_checked(I idx, long long n, int* err) {
+    return idx_ok((long long)idx, n, err) ? idx : I(0);
+}
 
 // Issues the copies of the halo tile; the caller waits (cp_async_wait_all,
 // then a barrier) before reading it.
-template <int Q, int V, typename T, bool LOAD_U>
+template <class Tl, typename T, bool LOAD_U>
 __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __restrict__ phi,
-                                          const T* __restrict__ u, T* s_phi, T* s_u, int x0, int y0, int z0) {
+                                          const T* __restrict__ u, T* s_phi, T* s_u, int x0, int y0, int z0,
+                                          int* err) {
     // one warp per halo row (fixed hy, hz): the row's periodic y/z image is
     // computed once, lanes walk the row's HX consecutive x positions
-    using Tl = Tile<Q, V>;
     constexpr int D = Tl::D;
     constexpr int ROWS = Tl::HY * Tl::HZ;
     constexpr int WARPS = Tl::THREADS / 32;
-    const int tid = threadIdx.x + Tl::TX * (threadIdx.y + Tl::TY * threadIdx.z);
+    const int tid = threadIdx.x + Tl::BX * (threadIdx.y + Tl::TY * threadIdx.z);
     const int warp = tid >> 5, lane = tid & 31;
     const int uplane = (int)P.plane;
     for (int r = warp; r < ROWS; r += WARPS) {
@@ -305,11 +367,12 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __res
         const int rowbase = P.px * (gy + P.ny * gz);
         const int sbase = Tl::HX * r + Tl::XO - 1;                 // slot of x0 - 1
         for (int e = lane; e < Tl::TX + 2; e += 32) {
-            const int node = rowbase + wrap_halo(x0 + e - 1, P.nx);
-            cp_async_value(s_phi + sbase + e, phi + node);
+            const int node = idx_checked(rowbase + wrap_halo(x0 + e - 1, P.nx), P.plane, err);
+            const int slot = idx_checked(sbase + e, Tl::HN, err);
+            cp_async_value(s_phi + slot, phi + node);
             if (LOAD_U) {
 #pragma unroll
-                for (int d = 0; d < D; ++d) cp_async_value(s_u + d * Tl::HN + sbase + e, u + d * uplane + node);
+                for (int d = 0; d < D; ++d) cp_async_value(s_u + d * Tl::HN + slot, u + d * uplane + node);
             }
         }
     }
@@ -320,10 +383,11 @@ __device__ __forceinline__ void load_halo(const StepParams<T>& P, const T* __res
 // ---------------------------------------------------------------------------
 template <int Q, typename T, typename S>
 __device__ __forceinline__ void phi_node(const StepParams<T>& P, const S* __restrict__ Bst,
-                                         const uint32_t* __restrict__ mask, T* __restrict__ phi, int x, int y, int z) {
+                                         const uint32_t* __restrict__ mask, T* __restrict__ phi, int x, int y, int z,
+                                         int* err) {
     using L = Lattice<Q>;
     if (x >= P.nx || y >= P.ny || z >= P.nz) return;
-    const int node = x + P.px * (y + P.ny * z);
+    const int node = idx_checked(x + P.px * (y + P.ny * z), P.plane, err);
     const uint32_t m = __ldg(mask + node);
     if (m & MASK_NOT_FLUID) return;
     const Wrap W(x, y, z, P.nx, P.ny, P.nz, P.px);
@@ -341,7 +405,7 @@ __device__ __forceinline__ void phi_node(const StepParams<T>& P, const S* __rest
     for (int i = 1; i < Q; ++i) {
         const int idx = ((m >> i) & 1u) ? (L::opp(i) - 1) * pl + node
                                         : (i - 1) * pl + node + W.off(-L::cx(i), -L::cy(i), -L::cz(i));
-        PS::accumulate(mv, idx, s);
+        PS::accumulate(mv, idx_checked(idx, (long long)(Q - 1) * pl, err), s);
     }
     if (PS::kShift) s = rest + (PS::kExact ? s : s * T(1.0 / kScaleB));
     // stored deviations B_i - chi_i/2 sum to phi - 1/2
@@ -350,12 +414,14 @@ __device__ __forceinline__ void phi_node(const StepParams<T>& P, const S* __rest
 
 template <int Q, typename T, typename S>
 __global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const S* __restrict__ Bst,
-                                                          const uint32_t* __restrict__ mask, T* __restrict__ phi) {
+                                                          const uint32_t* __restrict__ mask, T* __restrict__ phi,
+                                                          int* err) {
     using Tl = Tile<Q>;
     // tiles in the reverse of k_step's order: the B* that k_step wrote last is
     // still in L2 when this kernel starts
     const int bx = gridDim.x - 1 - blockIdx.x, by = gridDim.y - 1 - blockIdx.y, bz = gridDim.z - 1 - blockIdx.z;
-    phi_node<Q, T, S>(P, Bst, mask, phi, bx * Tl::TX + threadIdx.x, by * Tl::TY + threadIdx.y, bz * Tl::TZ + threadIdx.z);
+    phi_node<Q, T, S>(P, Bst, mask, phi, bx * Tl::TX + threadIdx.x, by * Tl::TY + threadIdx.y, bz * Tl::TZ + threadIdx.z,
+                      err);
 }
 
 // ---------------------------------------------------------------------------
@@ -367,12 +433,12 @@ __global__ void __launch_bounds__(Tile<Q>::THREADS) k_phi(StepParams<T> P, const
 template <int GK, typename T, int RULE>
 __global__ void __launch_bounds__(256) k_ghost(int64_t n_ghosts, const int32_t* __restrict__ g_node,
                                                const int32_t* __restrict__ g_corner, const T* __restrict__ g_wt,
-                                               T exp_eps, T eps, T* __restrict__ phi) {
+                                               T exp_eps, T eps, T* __restrict__ phi, int64_t plane, int* err) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= n_ghosts) return;
     T phiF = T(0);
 #pragma unroll
-    for (int k = 0; k < GK; ++k) phiF += g_wt[k * n_ghosts + g] * phi[g_corner[k * n_ghosts + g]];
+    for (int k = 0; k < GK; ++k) phiF += g_wt[k * n_ghosts + g] * phi[idx_checked(g_corner[k * n_ghosts + g], plane, err)];
     T phiG;
     if (RULE == 0) {
         phiG = phiF / (phiF + (T(1) - phiF) * exp_eps);
@@ -380,7 +446,8 @@ __global__ void __launch_bounds__(256) k_ghost(int64_t n_ghosts, const int32_t* 
         const T a = T(1) + T(0.5) * eps;
         phiG = T(4) * phiF / (a + sqrt(a * a - T(2) * eps * phiF)) - phiF;
     }
-    phi[g_node[g]] = phiG;
+    const int32_t gn = g_node[g];
+    if (idx_ok(gn, plane, err)) phi[gn] = phiG;
 }
 
 // ---------------------------------------------------------------------------
@@ -515,28 +582,222 @@ __device__ __forceinline__ void node_update_literal(const StepParams<double>& P,
 // come from the moving populations (Eq. pressureUpdate), so N[0] is not read.
 template <int Q, typename T, typename S>
 __device__ __forceinline__ void pull_streaming(const StepParams<T>& P, const S* __restrict__ Nin, int node, int x,
-                                               int y, int z, T (&N)[Q]) {
+                                               int y, int z, T (&N)[Q], int* err) {
     using L = Lattice<Q>;
     using PS = PopStore<S>;
     const Wrap Wr(x, y, z, P.nx, P.ny, P.nz, P.px);
     const int pl = (int)P.plane;
-    N[0] = PS::kShift ? T(0) : (T)PS::load_rest(PS::rest(Nin), node);
+    N[0] = PS::kShift ? T(0) : (T)PS::load_rest(PS::rest(Nin), idx_checked(node, P.plane, err));
     const auto* mv = PS::moving(Nin, pl);
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        N[i] = (T)PS::load_units(mv, (i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i)));
+        N[i] = (T)PS::load_units(mv, idx_checked((i - 1) * pl + node + Wr.off(-L::cx(i), -L::cy(i), -L::cz(i)),
+                                                 (long long)(Q - 1) * pl, err));
 }
 template <int Q, typename T, typename S>
 __device__ __forceinline__ void pull_bounce_back(const StepParams<T>& P, const S* __restrict__ Nin, uint32_t m,
-                                                 int node, T (&N)[Q]) {
+                                                 int node, T (&N)[Q], int* err) {
     using L = Lattice<Q>;
     using PS = PopStore<S>;
     const int pl = (int)P.plane;
     const auto* mv = PS::moving(Nin, pl);
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-        if ((m >> i) & 1u) N[i] = (T)PS::load_units(mv, (L::opp(i) - 1) * pl + node);
+        if ((m >> i) & 1u) N[i] = (T)PS::load_units(mv, idx_checked((L::opp(i) - 1) * pl + node,
+                                                                    (long long)(Q - 1) * pl, err));
 }
+
+// ---------------------------------------------------------------------------
+// Float arithmetic of one fluid node, shared by the one-node step kernel and
+// the two-node (pair) kernel, so that both round alike.  Inputs: the pulled
+// populations N (deviations, in storage units with FP16 storage), the color
+// phi at the node and the stencil sums gs[a] = sum_i w_i c_ia (phi_+ - phi_-)
+// over +/- pairs, ls = sum_i w_i (phi(x+c_i) - phi), us[a][b] likewise for u_b.
+// ---------------------------------------------------------------------------
+template <int Q, bool UNITS, bool CONTRAST>
+struct FloatNode {
+    using L = Lattice<Q>;
+    static constexpr int D = L::D;
+    static constexpr double w0 = L::w(0);
+    // storage units: times sN (N) and sB (B), 2^16 and 2^7 with FP16 storage,
+    // else 1.  Being powers of two, the scales fold into the per-node factors
+    // (omega1, the weights, phi, kseg) and the scaled values round exactly as
+    // the unscaled ones would.
+    static constexpr float sN = UNITS ? kScaleN : 1.0f, sB = UNITS ? kScaleB : 1.0f;
+    float phi, u[3], uu, p;
+    float F[3], gp[3];
+    float A0, A1, Axy, Axz, Ayz;               // stress projections of N - Neq, times (1 - 1/tau)
+    float base0, base1, base2, three_p, halfF;
+    float common1, common2, krc1, krc2;        // per direction class (1 axis, 2 diagonal/edge)
+    float phiB, phmB;
+
+    __device__ __forceinline__ void compute(const StepParams<float>& P, const float (&N)[Q], float phi_,
+                                            float (&gs)[3], float ls, float (&us)[3][3]) {
+        phi = phi_;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gp[a] = gs[a] * 3.0f;
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) us[a][bb] *= 3.0f;
+        }
+        const float lap = 6.0f * ls;
+
+        // mixture density and viscosity (Sec. II), relaxation time (Appendix A)
+        const float rho = P.rho_g + P.drho * phi;
+        const float inv_rho = rcp(rho);
+        const float nu = rcp(phi * P.inv_nu_l + (1.0f - phi) * P.inv_nu_g);
+        const float tau = 0.5f + 3.0f * nu;
+
+        // force-free velocity, moments and the pressure of this step (Eq. pressureUpdate)
+        float u0[3] = {0.f, 0.f, 0.f};
+        float sum_moving = 0.f;
+        float Pxx = 0.f, Pyy = 0.f, Pzz = 0.f, Pxy = 0.f, Pxz = 0.f, Pyz = 0.f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            // odd moments from N_i - N_opp, even ones from N_i + N_opp
+            if (L::opp(i) < i) continue;
+            const float sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
+            sum_moving += sp;
+            if (cx) { u0[0] += float(cx) * dp; Pxx += sp; }
+            if (cy) { u0[1] += float(cy) * dp; Pyy += sp; }
+            if (cz) { u0[2] += float(cz) * dp; Pzz += sp; }
+            if (cx * cy) Pxy += float(cx * cy) * sp;
+            if (cx * cz) Pxz += float(cx * cz) * sp;
+            if (cy * cz) Pyz += float(cy * cz) * sp;
+        }
+        // FP16 storage: N came in storage units (times 2^16); the moments are linear
+        // in N, so they are scaled back once (exactly, a power of two)
+        if constexpr (UNITS) {
+            constexpr float r = 1.0f / kScaleN;
+            sum_moving *= r;
+            Pxx *= r; Pyy *= r; Pzz *= r; Pxy *= r; Pxz *= r; Pyz *= r;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) u0[a] *= r;
+        }
+        // Eq. (pressureUpdate) takes sum_{i>0} N_i - (1 - chi_0) with the exact
+        // chi; the deviations are stored from the rounded chi of the storage, whose
+        // moving values sum to 1 - chi[0], so the difference of the two is
+        // chi_0 - chi[0], the rest class's correction (without it the float
+        // pressure would sit a constant ~4e-8 off, which F_p = -p grad(rho)
+        // turns into a velocity error at a density contrast)
+        const float pres_base = (sum_moving + P.chi_err[0]) * float(1.0 / 3.0);
+        const float inv_1mw0 = float(1.0 / (1.0 - w0));
+        const float uu0 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+        const float p0 = (pres_base - float(0.5 * w0) * uu0) * inv_1mw0;
+
+        // forces
+        const float muc = P.k48W * phi * (1.0f - phi) * (phi - 0.5f) + P.k3W2 * lap;   // chemical potential / sigma
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a] = (-P.sigma * muc) * gp[a] + rho * P.g[a];
+        if (D == 2) F[2] = 0.f;
+        if (CONTRAST) {
+            float gr[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) gr[a] = P.drho * gp[a];
+            const float kv = (tau - 0.5f) * float(1.0 / 3.0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                float sv = 0.f;
+#pragma unroll
+                for (int bb = 0; bb < D; ++bb) sv += (us[a][bb] + us[bb][a]) * gr[bb];
+                F[a] += kv * sv - p0 * gr[a];
+            }
+        }
+
+        // Eq. (velUpdate), Eq. (pressureUpdate)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = u0[a] + 0.5f * F[a] * inv_rho;
+        uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        p = (pres_base - float(0.5 * w0) * uu) * inv_1mw0;
+
+        // collision: traceless second moments of N - Neq, with sum Neq c c = (c2chi + p) I + u u
+        const float omega1 = UNITS ? (1.0f - rcp(tau)) * sN : 1.0f - rcp(tau);        // 1 - s_nu
+        if (D == 2) {
+            A0 = omega1 * ((Pxx - Pyy) - (u[0] * u[0] - u[1] * u[1])) * 0.25f;     // m7 . f / |m7|^2
+            A1 = 0.f;
+            Axy = omega1 * (Pxy - u[0] * u[1]) * 0.25f;                             // m8 . f / |m8|^2
+            Axz = Ayz = 0.f;
+        } else {
+            A0 = omega1 * ((2.0f * Pxx - Pyy - Pzz) - (2.0f * u[0] * u[0] - u[1] * u[1] - u[2] * u[2])) *
+                 float(1.0 / 36.0);
+            A1 = omega1 * ((Pyy - Pzz) - (u[1] * u[1] - u[2] * u[2])) * float(1.0 / 12.0);
+            Axy = omega1 * (Pxy - u[0] * u[1]) * 0.25f;
+            Axz = omega1 * (Pxz - u[0] * u[2]) * 0.25f;
+            Ayz = omega1 * (Pyz - u[1] * u[2]) * 0.25f;
+        }
+
+        // segregation: n_phi = grad phi / max(|grad phi|, 1e-6)
+        const float inv_gn = inv_norm_floor(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2], 1e-6f);
+        const float kseg = P.two_over_W * phi * (1.0f - phi) * inv_gn;
+        const float ksegB = UNITS ? kseg * sB : kseg;                       // recoloring in B's units
+        phiB = UNITS ? phi * (sB / sN) : phi;                               // phi N*, from N's units to B's
+        phmB = UNITS ? (phi - 0.5f) * sB : phi - 0.5f;
+        three_p = 3.0f * p;
+        halfF = 1.5f * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
+        base0 = 3.0f * u[0];
+        base1 = 3.0f * u[1];
+        base2 = 3.0f * u[2];
+        const float common = three_p - 1.5f * uu;
+        // per direction class (1 axis, 2 diagonal/edge): the equilibrium's constant
+        // part w_i (3p - 3u^2/2) + (chi_i - stored chi_i), divided by w_i, and the
+        // recolouring weight ksegB (chi_i + w_i 3p) with the exact chi_i
+        constexpr double kW1 = L::w(1), kW2 = L::w(D == 2 ? 5 : 7);
+        common1 = common + P.chi_err[1] * float(1.0 / kW1);
+        common2 = common + P.chi_err[2] * float(1.0 / kW2);
+        krc1 = ksegB * ((P.chi[1] + P.chi_err[1]) + float(kW1) * three_p);
+        krc2 = ksegB * ((P.chi[D == 2 ? 5 : 7] + P.chi_err[2]) + float(kW2) * three_p);
+    }
+
+    // Direction i (opp(i) > i) and its opposite o, in storage units: the
+    // post-collision N*_i - chi_i, N*_o - chi_o (they share the even part and
+    // flip the odd part) and B*_i - chi_i/2, B*_o - chi_o/2 with
+    // B* = phi N* + recolor, i.e. phi dN* + (phi - 1/2) chi_i + recolor.
+    __device__ __forceinline__ void dir(const StepParams<float>& P, int i, float& ni, float& no, float& bi,
+                                        float& bo) const {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const float wiN = float(L::w(i)) * sN;
+        float proj;
+        if (D == 2) {
+            proj = float(cx * cx - cy * cy) * A0 + float(cx * cy) * Axy;
+        } else {
+            const int c2 = cx * cx + cy * cy + cz * cz;
+            proj = float(3 * cx * cx - c2) * A0 + float(cy * cy - cz * cz) * A1 + float(cx * cy) * Axy +
+                   float(cx * cz) * Axz + float(cy * cz) * Ayz;
+        }
+        float cu3 = 0.f, cF = 0.f, cg = 0.f;   // 3 c.u, c.F, c.grad phi
+        if (cx) { cu3 += float(cx) * base0; cF += float(cx) * F[0]; cg += float(cx) * gp[0]; }
+        if (cy) { cu3 += float(cy) * base1; cF += float(cy) * F[1]; cg += float(cy) * gp[1]; }
+        if (cz) { cu3 += float(cz) * base2; cF += float(cz) * F[2]; cg += float(cz) * gp[2]; }
+        const bool axis = cx * cx + cy * cy + cz * cz == 1;
+        const float rc = (axis ? krc1 : krc2) * cg;                    // recoloring, odd in c
+        const float even = wiN * ((axis ? common1 : common2) + 0.5f * cu3 * cu3) + proj;
+        const float odd = wiN * (cu3 + halfF * cF);
+        ni = even + odd;
+        no = even - odd;
+        const float shift_b = phmB * P.chi[i];
+        bi = phiB * ni + shift_b + rc;
+        bo = phiB * no + shift_b - rc;
+    }
+
+    // Rest direction (no forcing, no stress projection, no recoloring, c_0 = 0),
+    // stored exactly (FP32): N*_0 - chi_0 and B*_0 - chi_0/2.
+    __device__ __forceinline__ float rest_N(const StepParams<float>& P) const {
+        return P.chi_err[0] - float(1.0 - w0) * three_p - float(1.5 * w0) * uu;
+    }
+    __device__ __forceinline__ float rest_B(const StepParams<float>& P, float nst0) const {
+        return phi * nst0 + (phi - 0.5f) * P.chi[0];
+    }
+    // With FP16 storage the float rest populations take the node totals the
+    // collision fixes less the moving populations as stored (sumN, sumB in
+    // storage units): sum_i (N*_i - chi_i) = 0 for any N, u, p and F (the
+    // equilibrium sums to sum chi = 1; the stress projection and the forcing
+    // have no zeroth moment) and sum_i (B*_i - chi_i/2) = phi - 1/2 (the
+    // recoloring is odd in c), so FP16 rounding moves no mass between the
+    // phases or out of the domain.
+    __device__ __forceinline__ static float rest_N_from_sum(float sumN) { return -sumN * (1.0f / kScaleN); }
+    __device__ __forceinline__ float rest_B_from_sum(float sumB) const { return (phi - 0.5f) - sumB * (1.0f / kScaleB); }
+};
 
 // One fluid node of the step: pulled populations N, the block's halo tile.
 template <int Q, int V, typename T, typename S, bool CONTRAST>
@@ -548,6 +809,9 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     constexpr int D = L::D;
     const int hc = (threadIdx.x + Tl::XO) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (D == 2 ? 0 : threadIdx.z + 1));
     const int pl = (int)P.plane;
+    int* const err = b.err;
+    // every store index below is a direction's plane offset plus this node
+    if (!idx_ok(node, P.plane, err)) return;
     using PS = PopStore<S>;
     constexpr bool kShift = PS::kShift;
 
@@ -556,7 +820,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     // against the FP64 oracle to 1e-12 over thousands of steps, sums in lattice
     // order as the definition is written.
     constexpr bool kPairs = sizeof(T) == 4;
-    const T phi = s_phi[hc];
+    const T phi = s_phi[idx_checked(hc, Tl::HN, err)];
     T gp[3] = {T(0), T(0), T(0)};
     T lsum = T(0);
     T du[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};   // du[a][b] = d_a u_b
@@ -569,7 +833,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
             const int hp = hc + Tl::off(cx, cy, cz), hm = hc - Tl::off(cx, cy, cz);
             // each difference enters every component it feeds with one
             // multiply-add by the constant c_ia w_i
-            const T pp = s_phi[hp], pm = s_phi[hm];
+            const T pp = s_phi[idx_checked(hp, Tl::HN, err)], pm = s_phi[idx_checked(hm, Tl::HN, err)];
             const T dphi = pp - pm;
             if (cx) gp[0] += (T(cx) * wi) * dphi;
             if (cy) gp[1] += (T(cy) * wi) * dphi;
@@ -578,7 +842,8 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
             if (CONTRAST) {
 #pragma unroll
                 for (int bb = 0; bb < D; ++bb) {
-                    const T dub = s_u[bb * Tl::HN + hp] - s_u[bb * Tl::HN + hm];
+                    const T dub = s_u[idx_checked(bb * Tl::HN + hp, D * Tl::HN, err)] -
+                                  s_u[idx_checked(bb * Tl::HN + hm, D * Tl::HN, err)];
                     if (cx) du[0][bb] += (T(cx) * wi) * dub;
                     if (cy) du[1][bb] += (T(cy) * wi) * dub;
                     if (cz) du[2][bb] += (T(cz) * wi) * dub;
@@ -586,7 +851,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
             }
         } else {
             const int h = hc + Tl::off(cx, cy, cz);
-            const T ph = s_phi[h];
+            const T ph = s_phi[idx_checked(h, Tl::HN, err)];
             gp[0] += wi * T(cx) * ph;
             gp[1] += wi * T(cy) * ph;
             if (D == 3) gp[2] += wi * T(cz) * ph;
@@ -594,7 +859,7 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
             if (CONTRAST) {
 #pragma unroll
                 for (int bb = 0; bb < D; ++bb) {
-                    const T ub = s_u[bb * Tl::HN + h];
+                    const T ub = s_u[idx_checked(bb * Tl::HN + h, D * Tl::HN, err)];
                     du[0][bb] += wi * T(cx) * ub;
                     du[1][bb] += wi * T(cy) * ub;
                     if (D == 3) du[2][bb] += wi * T(cz) * ub;
@@ -621,178 +886,129 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
         if (!(u[0] * u[0] + u[1] * u[1] + u[2] * u[2] < 1e30)) atomicOr(b.err, kErrNonFinite);
         return;
     } else {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        gp[a] *= T(3);
-#pragma unroll
-        for (int bb = 0; bb < 3; ++bb) du[a][bb] *= T(3);
-    }
-    const T lap = T(6) * lsum;
-
-    // mixture density and viscosity (Sec. II), relaxation time (Appendix A)
-    const T rho = P.rho_g + P.drho * phi;
-    const T inv_rho = rcp(rho);
-    const T nu = rcp(phi * P.inv_nu_l + (T(1) - phi) * P.inv_nu_g);
-    const T tau = T(0.5) + T(3) * nu;
-
-    // force-free velocity, moments and the pressure of this step (Eq. pressureUpdate)
     static_assert(kPairs && kShift, "float arithmetic runs on deviations, summed over +/- pairs");
-    T u0[3] = {T(0), T(0), T(0)};
-    T sum_moving = T(0);
-    T Pxx = T(0), Pyy = T(0), Pzz = T(0), Pxy = T(0), Pxz = T(0), Pyz = T(0);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        // odd moments from N_i - N_opp, even ones from N_i + N_opp
-        if (L::opp(i) < i) continue;
-        const T sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
-        sum_moving += sp;
-        if (cx) { u0[0] += T(cx) * dp; Pxx += sp; }
-        if (cy) { u0[1] += T(cy) * dp; Pyy += sp; }
-        if (cz) { u0[2] += T(cz) * dp; Pzz += sp; }
-        if (cx * cy) Pxy += T(cx * cy) * sp;
-        if (cx * cz) Pxz += T(cx * cz) * sp;
-        if (cy * cz) Pyz += T(cy * cz) * sp;
-    }
-    // FP16 storage: N came in storage units (times 2^16); the moments are linear
-    // in N, so they are scaled back once (exactly, a power of two)
     constexpr bool kUnits = !PS::kExact;
-    if constexpr (kUnits) {
-        constexpr T r = T(1.0 / kScaleN);
-        sum_moving *= r;
-        Pxx *= r; Pyy *= r; Pzz *= r; Pxy *= r; Pxz *= r; Pyz *= r;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) u0[a] *= r;
-    }
-    // sum_{i>0} chi_i = 1 - chi_0: with deviations the chi part is already gone
-    const T pres_base = kShift ? sum_moving * T(1.0 / 3.0) : (sum_moving - (T(1) - P.chi[0])) * T(1.0 / 3.0);
-    const T inv_1mw0 = T(1.0 / (1.0 - w0));
-    const T uu0 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
-    const T p0 = (pres_base - T(0.5 * w0) * uu0) * inv_1mw0;
-
-    // forces
-    const T muc = P.k48W * phi * (T(1) - phi) * (phi - T(0.5)) + P.k3W2 * lap;   // chemical potential / sigma
-    T F[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) F[a] = (-P.sigma * muc) * gp[a] + rho * P.g[a];
-    if (D == 2) F[2] = T(0);
-    if (CONTRAST) {
-        T gr[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gr[a] = P.drho * gp[a];
-        const T kv = (tau - T(0.5)) * T(1.0 / 3.0);
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            T sv = T(0);
-#pragma unroll
-            for (int bb = 0; bb < D; ++bb) sv += (du[a][bb] + du[bb][a]) * gr[bb];
-            F[a] += kv * sv - p0 * gr[a];
-        }
-    }
-
-    // Eq. (velUpdate), Eq. (pressureUpdate)
-    T u[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = u0[a] + T(0.5) * F[a] * inv_rho;
-    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const T p = (pres_base - T(0.5 * w0) * uu) * inv_1mw0;
-
-    // collision: traceless second moments of N - Neq, with sum Neq c c = (c2chi + p) I + u u
-    // Populations are produced in storage units: times sN (N) and sB (B), 2^16
-    // and 2^7 with FP16 storage, else 1.  Being powers of two, the scales fold
-    // into the per-node factors below (omega1, the weights, phi, kseg) and the
-    // scaled values round exactly as the unscaled ones would.
-    constexpr T sN = kUnits ? T(kScaleN) : T(1), sB = kUnits ? T(kScaleB) : T(1);
-    const T omega1 = kUnits ? (T(1) - rcp(tau)) * sN : T(1) - rcp(tau);        // 1 - s_nu
-    T A0, A1, Axy, Axz, Ayz;
-    if (D == 2) {
-        A0 = omega1 * ((Pxx - Pyy) - (u[0] * u[0] - u[1] * u[1])) * T(0.25);     // m7 . f / |m7|^2
-        A1 = T(0);
-        Axy = omega1 * (Pxy - u[0] * u[1]) * T(0.25);                             // m8 . f / |m8|^2
-        Axz = Ayz = T(0);
-    } else {
-        A0 = omega1 * ((T(2) * Pxx - Pyy - Pzz) - (T(2) * u[0] * u[0] - u[1] * u[1] - u[2] * u[2])) * T(1.0 / 36.0);
-        A1 = omega1 * ((Pyy - Pzz) - (u[1] * u[1] - u[2] * u[2])) * T(1.0 / 12.0);
-        Axy = omega1 * (Pxy - u[0] * u[1]) * T(0.25);
-        Axz = omega1 * (Pxz - u[0] * u[2]) * T(0.25);
-        Ayz = omega1 * (Pyz - u[1] * u[2]) * T(0.25);
-    }
-
-    // segregation: n_phi = grad phi / max(|grad phi|, 1e-6)
-    const T inv_gn = inv_norm_floor(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2], T(1e-6));
-    const T kseg = P.two_over_W * phi * (T(1) - phi) * inv_gn;
-    const T ksegB = kUnits ? kseg * sB : kseg;                       // recoloring in B's units
-    const T phiB = kUnits ? phi * (sB / sN) : phi;                   // phi N*, from N's units to B's
-    const T phmB = kUnits ? (phi - T(0.5)) * sB : phi - T(0.5);
-    const T three_p = T(3) * p;
-    const T halfF = T(1.5) * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
-    const T base0 = T(3) * u[0], base1 = T(3) * u[1], base2 = T(3) * u[2];
-    const T common = three_p - T(1.5) * uu;
+    FloatNode<Q, kUnits, CONTRAST> nd;
+    nd.compute(P, N, phi, gp, lsum, du);
 
     // u and p: FP16 storage writes them before the populations, which frees
     // their registers for the stored sums (no spills in the batched kernels);
     // FP32 writes them last, measured 0.7% faster
     auto store_u_p = [&]() {
 #pragma unroll
-        for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = u[a];
-        b.p[node] = p;
-        if (!(uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
+        for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = nd.u[a];
+        b.p[node] = nd.p;
+        if (!(nd.uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
     };
     if constexpr (!PS::kExact) store_u_p();
 
     auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
     auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
-    // rest direction: no forcing, no stress projection, no recoloring (c_0 = 0)
     if constexpr (PS::kExact) {
-        const T nst0 = T(0) - T(1.0 - w0) * three_p - T(1.5 * w0) * uu;
+        const T nst0 = nd.rest_N(P);
         PS::store_rest(PS::rest(b.Nout), node, nst0);
-        PS::store_rest(PS::rest(b.Bout), node, phi * nst0 + (phi - T(0.5)) * P.chi[0]);
+        PS::store_rest(PS::rest(b.Bout), node, nd.rest_B(P, nst0));
     }
     // sums of the moving populations as stored (FP16 storage)
     T sumN = T(0), sumB = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        // direction i and its opposite share the even part and flip the odd part
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
-        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const T wi = T(L::w(i)), wiN = T(L::w(i)) * sN;
-        T proj;
-        if (D == 2) {
-            proj = T(cx * cx - cy * cy) * A0 + T(cx * cy) * Axy;
-        } else {
-            const int c2 = cx * cx + cy * cy + cz * cz;
-            proj = T(3 * cx * cx - c2) * A0 + T(cy * cy - cz * cz) * A1 + T(cx * cy) * Axy + T(cx * cz) * Axz +
-                   T(cy * cz) * Ayz;
-        }
-        T cu3 = T(0), cF = T(0), cg = T(0);   // 3 c.u, c.F, c.grad phi
-        if (cx) { cu3 += T(cx) * base0; cF += T(cx) * F[0]; cg += T(cx) * gp[0]; }
-        if (cy) { cu3 += T(cy) * base1; cF += T(cy) * F[1]; cg += T(cy) * gp[1]; }
-        if (cz) { cu3 += T(cz) * base2; cF += T(cz) * F[2]; cg += T(cz) * gp[2]; }
-        const T rc = ksegB * cg * (P.chi[i] + wi * three_p);     // recoloring, odd in c
-        const T even = wiN * (common + T(0.5) * cu3 * cu3) + proj;
-        const T odd = wiN * (cu3 + halfF * cF);
-        const T ni = even + odd, no = even - odd;
-        // B* = phi N* + recolor, stored as B* - chi_i/2 = phi dN* + (phi - 1/2) chi_i + recolor
-        const T shift_b = phmB * P.chi[i];
+        T ni, no, bi, bo;
+        nd.dir(P, i, ni, no, bi, bo);
         PS::store_units(Nmov, (i - 1) * pl + node, ni, sumN);
         PS::store_units(Nmov, (o - 1) * pl + node, no, sumN);
-        PS::store_units(Bmov, (i - 1) * pl + node, phiB * ni + shift_b + rc, sumB);
-        PS::store_units(Bmov, (o - 1) * pl + node, phiB * no + shift_b - rc, sumB);
+        PS::store_units(Bmov, (i - 1) * pl + node, bi, sumB);
+        PS::store_units(Bmov, (o - 1) * pl + node, bo, sumB);
     }
     if constexpr (!PS::kExact) {
-        // The collision keeps each node's population totals: sum_i (N*_i - chi_i)
-        // = 0 for any N, u, p and F (the equilibrium sums to sum chi = 1; the
-        // stress projection and the forcing have no zeroth moment), and
-        // sum_i (B*_i - chi_i/2) = phi - 1/2 (the recoloring is odd in c).  The
-        // float rest populations are written as those totals less the rounded
-        // moving populations, so FP16 rounding moves no mass between the phases
-        // or out of the domain.
-        PS::store_rest(PS::rest(b.Nout), node, -sumN * T(1.0 / kScaleN));
-        PS::store_rest(PS::rest(b.Bout), node, (phi - T(0.5)) - sumB * T(1.0 / kScaleB));
+        PS::store_rest(PS::rest(b.Nout), node, FloatNode<Q, kUnits, CONTRAST>::rest_N_from_sum(sumN));
+        PS::store_rest(PS::rest(b.Bout), node, nd.rest_B_from_sum(sumB));
     }
     if constexpr (PS::kExact) store_u_p();
     }
+}
+
+// A block's halo tile (color, and the previous velocity with a density
+// contrast) with a one-node ring: issued by halo_issue, waited for by
+// halo_complete, shared by the step kernels of every tile shape.  With maps
+// (tiles whose halo needs no periodic image in y and z) two tiled TMA copies
+// fill it, completed on the mbarrier `bar`; at the x ends of the grid the box
+// reads zeros where x < 0 or x >= nx, and the stencil needs the periodic
+// images of x = -1 and x = nx there: one thread per halo row and field loads
+// such a value now and writes it once the copy has landed (fix_at >= 0).
+// Without maps the halo is copied element by element with cp.async.
+// halo_issue returns false when the debug bounds checks reject the tile's box.
+template <class Tl, typename T, typename S, bool CONTRAST>
+__device__ __forceinline__ bool halo_issue(const StepParams<T>& P, const StepBuffers<T, S>& b, T* s_phi, T* s_u,
+                                           int x0, int y0, int z0, const CUtensorMap* tm_phi,
+                                           const CUtensorMap* tm_u, uint64_t* bar, T& fix_v, int& fix_at) {
+    const bool tma = tm_phi != nullptr;
+    fix_v = T(0);
+    fix_at = -1;
+    constexpr int kHaloFields = CONTRAST ? 1 + Tl::D : 1;
+    if (tma && kDebugBounds) {
+        // the box of a tiled copy: x origin on a 16-byte boundary, the whole
+        // halo inside the grid in y and z (no periodic image needed there)
+        const bool box_ok = ((x0 - Tl::XO) & 3) == 0 && y0 >= 1 && y0 + Tl::TY + 1 <= P.ny &&
+                            (Tl::D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= P.nz));
+        if (!box_ok) {
+            if (threadIdx.x + threadIdx.y + threadIdx.z == 0) atomicOr(b.err, kErrBounds);
+            return false;                                  // the whole block takes this branch
+        }
+    }
+    if (tma) {
+        const int tid = threadIdx.x + Tl::BX * (threadIdx.y + Tl::TY * threadIdx.z);
+        if (tid == 0) {
+            constexpr unsigned kBytes = (CONTRAST ? 1 + Tl::D : 1) * Tl::HN * sizeof(T);
+            mbar_expect_tx(bar, kBytes);
+            const int zc = Tl::D == 2 ? 0 : z0 - 1;
+            tma_load_3d(s_phi, tm_phi, x0 - Tl::XO, y0 - 1, zc, bar);
+            if (CONTRAST) tma_load_4d(s_u, tm_u, x0 - Tl::XO, y0 - 1, zc, 0, bar);
+        }
+        const bool lo = x0 == 0, hi = x0 + Tl::TX >= P.nx;
+        constexpr int kRows = Tl::HY * Tl::HZ, kPerCol = kRows * kHaloFields;
+        // one thread per periodic image to patch: both x ends of a one-tile-wide grid at once
+        static_assert(Tl::THREADS >= 2 * kPerCol, "too few threads to patch the x-end halo columns");
+        if ((lo || hi) && tid < (int(lo) + int(hi)) * kPerCol) {
+            const bool left = lo && tid < kPerCol;              // x = -1, else x = nx
+            const int k = tid % kPerCol, field = k / kRows, r = k % kRows;
+            const int hy = r % Tl::HY, hz = r / Tl::HY;
+            const int gz = Tl::D == 2 ? 0 : z0 - 1 + hz;
+            const int node = (left ? P.nx - 1 : 0) + P.px * (y0 - 1 + hy + P.ny * gz);
+            const int fn = idx_checked(node, P.plane, b.err);
+            fix_v = field == 0 ? b.phi[fn] : b.u_in[(field - 1) * (int)P.plane + fn];
+            fix_at = (field == 0 ? 0 : Tl::HN * field) + (left ? Tl::XO - 1 : P.nx - x0 + Tl::XO) + Tl::HX * r;
+            if (!idx_ok(fix_at, kHaloFields * Tl::HN, b.err)) fix_at = -1;
+        }
+    } else {
+        load_halo<Tl, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0, b.err);
+    }
+    return true;
+}
+
+// Waits for the halo issued by halo_issue and patches the x-end images;
+// false if a tiled copy did not complete within the bounded wait.  The
+// caller's barrier follows.
+template <class Tl, typename T, typename S>
+__device__ __forceinline__ bool halo_complete(const StepBuffers<T, S>& b, bool tma, uint64_t* bar, T* s_phi,
+                                              T* s_u, T fix_v, int fix_at) {
+    if (!tma) {
+        cp_async_wait_all();
+        return true;
+    }
+    const bool halo_ok = mbar_wait(bar, 0);
+    if (!halo_ok) {
+        // the tile is skipped and the host is told (LBM_ERR_TIMEOUT; the domain
+        // is refused further steps).  The copy may still be in flight into
+        // this block's shared memory: wait for it once more, again bounded,
+        // before the block exits, so that it does not land in a later block.
+        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) atomicOr(b.err, kErrCopyTimeout);
+        mbar_wait(bar, 0);
+    }
+    if (halo_ok && fix_at >= 0) (fix_at < Tl::HN ? s_phi : s_u - Tl::HN)[fix_at] = fix_v;
+    return halo_ok;
 }
 
 // The tile at (x0, y0, z0): the halo copies are issued first, then every
@@ -803,54 +1019,19 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
                                           int x0, int y0, int z0, const CUtensorMap* tm_phi = nullptr,
                                           const CUtensorMap* tm_u = nullptr, uint64_t* bar = nullptr) {
     using Tl = Tile<Q, V>;
-    // the halo by two tiled TMA copies when maps are given (interior tiles),
-    // else element by element with cp.async
     const bool tma = tm_phi != nullptr;
-    // At the x ends of the grid the box reads zeros where x < 0 or x >= nx; the
-    // stencil needs the periodic images of x = -1 and x = nx there: one thread
-    // per halo row and field loads such a value now and writes it once the
-    // copy has landed (fix_at >= 0).
-    T fix_v = T(0);
-    int fix_at = -1;
-    if (tma) {
-        const int tid = threadIdx.x + Tl::TX * (threadIdx.y + Tl::TY * threadIdx.z);
-        if (tid == 0) {
-            constexpr unsigned kBytes = (CONTRAST ? 1 + Tl::D : 1) * Tl::HN * sizeof(T);
-            mbar_expect_tx(bar, kBytes);
-            const int zc = Tl::D == 2 ? 0 : z0 - 1;
-            tma_load_3d(s_phi, tm_phi, x0 - Tl::XO, y0 - 1, zc, bar);
-            if (CONTRAST) tma_load_4d(s_u, tm_u, x0 - Tl::XO, y0 - 1, zc, 0, bar);
-        }
-        const bool lo = x0 == 0, hi = x0 + Tl::TX >= P.nx;
-        constexpr int kRows = Tl::HY * Tl::HZ, kPerCol = kRows * (CONTRAST ? 1 + Tl::D : 1);
-        if ((lo || hi) && tid < (int(lo) + int(hi)) * kPerCol) {
-            const bool left = lo && tid < kPerCol;              // x = -1, else x = nx
-            const int k = tid % kPerCol, field = k / kRows, r = k % kRows;
-            const int hy = r % Tl::HY, hz = r / Tl::HY;
-            const int gz = Tl::D == 2 ? 0 : z0 - 1 + hz;
-            const int node = (left ? P.nx - 1 : 0) + P.px * (y0 - 1 + hy + P.ny * gz);
-            fix_v = field == 0 ? b.phi[node] : b.u_in[(field - 1) * (int)P.plane + node];
-            fix_at = (field == 0 ? 0 : Tl::HN * field) + (left ? Tl::XO - 1 : P.nx - x0 + Tl::XO) + Tl::HX * r;
-        }
-    } else {
-        load_halo<Q, V, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0);
-    }
+    T fix_v;
+    int fix_at;
+    if (!halo_issue<Tl, T, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, tm_phi, tm_u, bar, fix_v, fix_at)) return;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     const bool in_grid = x < P.nx && y < P.ny && z < P.nz;
-    const int node = in_grid ? x + P.px * (y + P.ny * z) : 0;
+    const int node = in_grid ? idx_checked(x + P.px * (y + P.ny * z), P.plane, b.err) : 0;
     const uint32_t m = in_grid ? __ldg(b.mask + node) : MASK_NOT_FLUID;
     T N[Q];
-    if (in_grid) pull_streaming<Q, T, S>(P, b.Nin, node, x, y, z, N);      // in flight with the mask load
+    if (in_grid) pull_streaming<Q, T, S>(P, b.Nin, node, x, y, z, N, b.err);      // in flight with the mask load
     const bool fluid = !(m & MASK_NOT_FLUID);
-    if (fluid && (m & ~MASK_NOT_FLUID)) pull_bounce_back<Q, T, S>(P, b.Nin, m, node, N);
-    bool halo_ok = true;
-    if (tma) {
-        halo_ok = mbar_wait(bar, 0);
-        if (!halo_ok && threadIdx.x + threadIdx.y + threadIdx.z == 0) atomicOr(b.err, kErrCopyTimeout);
-        if (fix_at >= 0) (fix_at < Tl::HN ? s_phi : s_u - Tl::HN)[fix_at] = fix_v;
-    } else {
-        cp_async_wait_all();
-    }
+    if (fluid && (m & ~MASK_NOT_FLUID)) pull_bounce_back<Q, T, S>(P, b.Nin, m, node, N, b.err);
+    const bool halo_ok = halo_complete<Tl, T, S>(b, tma, bar, s_phi, s_u, fix_v, fix_at);
     __syncthreads();
     if (fluid && halo_ok) step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, N, node);
 }
@@ -916,9 +1097,9 @@ struct BatchEntry {
 template <typename T, typename S>
 __constant__ BatchEntry<T, S> c_batch[kBatchSlots];
 
-// maps: tiled TMA maps of the halo fields, three per slot (phi, then u_in for
-// step parity 0 and 1), in global memory; used with tile shape 0 (the shape
-// the maps' boxes are made for) on tiles needing no periodic image in y, z.
+// maps: tiled TMA maps of the halo fields for this tile shape, three per slot
+// (phi, then u_in for step parity 0 and 1, with the box of Tile<Q, V>'s halo),
+// in global memory; used on tiles needing no periodic image in y, z.
 template <int Q, typename T, typename S, int V, bool CONTRAST>
 __global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Tile<Q, V>::THREADS>()))
     k_step_batched(const int4* __restrict__ tiles, const CUtensorMap* __restrict__ maps, int parity) {
@@ -927,9 +1108,12 @@ __global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Ti
     __shared__ __align__(128) T s_u[CONTRAST ? Tl::D * Tl::HN : 1];
     __shared__ __align__(8) uint64_t s_bar;
     const int4 t = __ldg(tiles + blockIdx.x);          // {slot, x0, y0, z0}
-    const BatchEntry<T, S>& e = c_batch<T, S>[t.x];
+    const BatchEntry<T, S>& e = c_batch<T, S>[idx_checked(t.x, kBatchSlots, c_batch<T, S>[0].b[0].err)];
     const int y0 = t.z, z0 = t.w;
-    const bool tma = V == 0 && maps != nullptr && e.tma && y0 >= 1 && y0 + Tl::TY + 1 <= e.P.ny &&
+    if (kDebugBounds && !(idx_ok(t.y, e.P.nx, e.b[0].err) && idx_ok(y0, e.P.ny, e.b[0].err) &&
+                          idx_ok(z0, e.P.nz, e.b[0].err)))
+        return;                                         // a tile outside its domain
+    const bool tma = maps != nullptr && e.tma && y0 >= 1 && y0 + Tl::TY + 1 <= e.P.ny &&
                      (Tl::D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= e.P.nz));
     if (tma) {
         if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
@@ -944,10 +1128,10 @@ __global__ void __launch_bounds__(Tile<Q, V>::THREADS, (step_min_blocks<T, S, Ti
 template <int Q, typename T, typename S, int V>
 __global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_phi_batched(const int4* __restrict__ tiles, int parity) {
     const int4 t = __ldg(tiles + (gridDim.x - 1 - blockIdx.x));     // reverse order, as k_phi
-    const BatchEntry<T, S>& e = c_batch<T, S>[t.x];
+    const BatchEntry<T, S>& e = c_batch<T, S>[idx_checked(t.x, kBatchSlots, c_batch<T, S>[0].b[0].err)];
     // this step's output B* is the buffer the step kernel wrote
     phi_node<Q, T, S>(e.P, e.b[parity].Bout, e.b[parity].mask, e.b[parity].phi, t.y + threadIdx.x, t.z + threadIdx.y,
-                      t.w + threadIdx.z);
+                      t.w + threadIdx.z, e.b[parity].err);
 }
 
 // Ghost tables of all domains: ghost g of the batch belongs to the domain d with
@@ -961,6 +1145,8 @@ struct GhostTable {
     T exp_eps, eps;
     T* phi;
     int rule;
+    int64_t plane;                 // entries of phi (bounds of node and corner indices)
+    int* err;                      // the domain's error word
 };
 
 template <int GK, typename T>
@@ -977,9 +1163,10 @@ __global__ void __launch_bounds__(256) k_ghost_batched(const GhostTable<T>* __re
     const GhostTable<T>& t = tabs[lo];
     const int64_t k = g - ghost_begin[lo];
     const int64_t n = t.n;
+    if (!idx_ok(k, n, t.err)) return;
     T phiF = T(0);
 #pragma unroll
-    for (int c = 0; c < GK; ++c) phiF += t.wt[c * n + k] * t.phi[t.corner[c * n + k]];
+    for (int c = 0; c < GK; ++c) phiF += t.wt[c * n + k] * t.phi[idx_checked(t.corner[c * n + k], t.plane, t.err)];
     T phiG;
     if (t.rule == 0) {
         phiG = phiF / (phiF + (T(1) - phiF) * t.exp_eps);
@@ -987,7 +1174,8 @@ __global__ void __launch_bounds__(256) k_ghost_batched(const GhostTable<T>* __re
         const T a = T(1) + T(0.5) * t.eps;
         phiG = T(4) * phiF / (a + sqrt(a * a - T(2) * t.eps * phiF)) - phiF;
     }
-    t.phi[t.node[k]] = phiG;
+    const int32_t gn = t.node[k];
+    if (idx_ok(gn, t.plane, t.err)) t.phi[gn] = phiG;
 }
 
 }  // namespace lbmgpu

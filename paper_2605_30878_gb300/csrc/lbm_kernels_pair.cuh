@@ -1,0 +1,210 @@
+// Two-node step kernel (float arithmetic, FP32 or FP16 population storage).
+//
+// Every thread updates the two x-adjacent nodes A = (x0 + 2t, y, z) and
+// B = (x0 + 2t + 1, y, z) of its row, with the arithmetic of k_step: the same
+// stencil sums in the same order and FloatNode's per-node update, so the two
+// kernels round alike.  Since A's index is even, the pair shares
+//   - its mask (one 8-byte load),
+//   - its streaming pulls along y and z (one two-wide load per direction with
+//     c_x = 0; directions with c_x != 0 pull from odd offsets, two loads),
+//   - its shared-memory stencil values (two-wide loads; the rows a +/- x
+//     direction needs come from three aligned two-wide loads, shared by the
+//     directions of that row),
+//   - its stores of N*, B*, u and p (one two-wide store each),
+// which halves the load/store and address instructions per node of the
+// one-node kernel.  Blocks are 32 x TY x TZ threads covering 64 x TY x TZ
+// nodes; the halo tile is copied by the same halo_issue/halo_complete as
+// k_step's (TMA boxes 72 x (TY + 2) x (TZ + 2) on interior tiles).  A node of
+// the pair that is not fluid gets zero velocity and pressure; its population
+// slots receive values that nothing reads (every pull of a fluid node reads
+// fluid sources or its own slots, as the diagnostics and state transfer do).
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbmgpu {
+
+template <int Q>
+struct PairTile {
+    static constexpr int D = Lattice<Q>::D;
+    static constexpr int BX = 32;                  // threads along x
+    static constexpr int TX = 2 * BX;              // nodes along x
+    static constexpr int TY = D == 2 ? 4 : 2;
+    static constexpr int TZ = D == 2 ? 1 : 2;
+    static constexpr int XO = 4;                   // halo origin x0 - 4: 16-byte aligned for tiled copies
+    static constexpr int HX = TX + 2 * XO;
+    static constexpr int HY = TY + 2;
+    static constexpr int HZ = D == 2 ? 1 : TZ + 2;
+    static constexpr int HN = HX * HY * HZ;
+    static constexpr int THREADS = BX * TY * TZ;
+    __host__ __device__ static constexpr int off(int cx, int cy, int cz) { return cx + HX * (cy + HY * cz); }
+};
+
+// Resident blocks per SM the pair kernel is compiled for (registers per
+// thread <= 65536 / (THREADS * blocks)).
+constexpr int kPairBlocks = 5;
+
+// The values at halo slots hc + o and hc + o + 1 (hc even): one aligned
+// two-wide load for even o, else the odd half of the pair below and the even
+// half of the pair above (loads of the same address are shared by the compiler
+// across directions).
+template <int HN>
+__device__ __forceinline__ float2 halo_pair(const float* s, int hc, int o, int* err) {
+    if ((o & 1) == 0) return *reinterpret_cast<const float2*>(s + idx_checked(hc + o, HN - 1, err));
+    const float2 lo = *reinterpret_cast<const float2*>(s + idx_checked(hc + o - 1, HN - 1, err));
+    const float2 hi = *reinterpret_cast<const float2*>(s + idx_checked(hc + o + 1, HN - 1, err));
+    return make_float2(lo.y, hi.x);
+}
+
+template <int Q, typename S, bool CONTRAST>
+__global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
+    k_step_pair(StepParams<float> P, StepBuffers<float, S> b, const __grid_constant__ CUtensorMap tm_phi,
+                const __grid_constant__ CUtensorMap tm_u, int tma) {
+    using Tl = PairTile<Q>;
+    using L = Lattice<Q>;
+    using PS = PopStore<S>;
+    constexpr int D = L::D;
+    constexpr bool kUnits = !PS::kExact;
+    __shared__ __align__(128) float s_phi[Tl::HN];
+    __shared__ __align__(128) float s_u[CONTRAST ? D * Tl::HN : 2];
+    __shared__ __align__(8) uint64_t s_bar;
+    int* const err = b.err;
+    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
+    // tiles whose halo needs no periodic image in y and z (x images are patched)
+    const bool interior = tma && y0 >= 1 && y0 + Tl::TY + 1 <= P.ny &&
+                          (D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= P.nz));
+    if (interior) {
+        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
+        __syncthreads();                                      // the barrier exists before anyone waits on it
+    }
+    float fix_v;
+    int fix_at;
+    if (!halo_issue<Tl, float, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, interior ? &tm_phi : nullptr, &tm_u,
+                                            &s_bar, fix_v, fix_at))
+        return;
+
+    // the pair's populations, pulled while the halo is in flight
+    const int xa = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    const bool in_grid = xa < P.nx && y < P.ny && z < P.nz;      // A; B may be a padding column
+    const bool b_in = in_grid && xa + 1 < P.nx;
+    const int nodeA = in_grid ? idx_checked(xa + P.px * (y + P.ny * z), P.plane - 1, err) : 0;
+    uint2 m = make_uint2(MASK_NOT_FLUID, MASK_NOT_FLUID);
+    if (in_grid) m = __ldg(reinterpret_cast<const uint2*>(b.mask + nodeA));
+    const bool fluidA = !(m.x & MASK_NOT_FLUID), fluidB = !(m.y & MASK_NOT_FLUID);
+    const int pl = (int)P.plane;
+    const long long nmv = (long long)(Q - 1) * pl;
+    const auto* mv = PS::moving(b.Nin, pl);
+    float NA[Q], NB[Q];
+    NA[0] = NB[0] = 0.f;                          // the deviation form never reads the rest population
+    if (in_grid) {
+        const Wrap W(xa, y, z, P.nx, P.ny, P.nz, P.px);
+        const int xpB = (xa + 1 == P.nx - 1) ? 1 - P.nx : 1;    // B (x >= 1) never wraps to the left
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const int row = (i - 1) * pl + nodeA + W.off(0, -cy, -cz);
+            if (cx == 0) {
+                const float2 v = PS::load_units2(mv, idx_checked(row, nmv - 1, err));
+                NA[i] = v.x;
+                NB[i] = v.y;
+            } else if (cx > 0) {                  // from x - 1: A's may wrap, B's is A's own column
+                NA[i] = (float)PS::load_units(mv, idx_checked(row + W.xm, nmv, err));
+                NB[i] = (float)PS::load_units(mv, idx_checked(b_in ? row : row + W.xm, nmv, err));
+            } else {                              // from x + 1
+                NA[i] = (float)PS::load_units(mv, idx_checked(row + W.xp, nmv, err));
+                NB[i] = (float)PS::load_units(mv, idx_checked(b_in ? row + 1 + xpB : row + W.xp, nmv, err));
+            }
+        }
+        // halfway bounce-back: directions whose neighbour is not fluid read the node's own opposite slot
+        if (fluidA && (m.x & ~MASK_NOT_FLUID)) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i)
+                if ((m.x >> i) & 1u)
+                    NA[i] = (float)PS::load_units(mv, idx_checked((L::opp(i) - 1) * pl + nodeA, nmv, err));
+        }
+        if (fluidB && (m.y & ~MASK_NOT_FLUID)) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i)
+                if ((m.y >> i) & 1u)
+                    NB[i] = (float)PS::load_units(mv, idx_checked((L::opp(i) - 1) * pl + nodeA + 1, nmv, err));
+        }
+    }
+    const bool halo_ok = halo_complete<Tl, float, S>(b, interior, &s_bar, s_phi, s_u, fix_v, fix_at);
+    __syncthreads();
+    if (!(fluidA || fluidB) || !halo_ok) return;
+
+    // isotropic stencils of both nodes, over +/- pairs in the order of k_step
+    const int hcA = (2 * threadIdx.x + Tl::XO) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (D == 2 ? 0 : threadIdx.z + 1));
+    const float2 ph = halo_pair<Tl::HN>(s_phi, hcA, 0, err);
+    float gA[3] = {0.f, 0.f, 0.f}, gB[3] = {0.f, 0.f, 0.f};
+    float lA = 0.f, lB = 0.f;
+    float dA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float dB[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const float wi = float(L::w(i));
+        const int o = Tl::off(cx, cy, cz);
+        const float2 pp = halo_pair<Tl::HN>(s_phi, hcA, o, err), pm = halo_pair<Tl::HN>(s_phi, hcA, -o, err);
+        const float dphiA = pp.x - pm.x, dphiB = pp.y - pm.y;
+        if (cx) { gA[0] += (float(cx) * wi) * dphiA; gB[0] += (float(cx) * wi) * dphiB; }
+        if (cy) { gA[1] += (float(cy) * wi) * dphiA; gB[1] += (float(cy) * wi) * dphiB; }
+        if (cz) { gA[2] += (float(cz) * wi) * dphiA; gB[2] += (float(cz) * wi) * dphiB; }
+        lA += wi * ((pp.x - ph.x) + (pm.x - ph.x));
+        lB += wi * ((pp.y - ph.y) + (pm.y - ph.y));
+        if (CONTRAST) {
+#pragma unroll
+            for (int bb = 0; bb < D; ++bb) {
+                const float2 up = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, o, err);
+                const float2 um = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, -o, err);
+                const float duA = up.x - um.x, duB = up.y - um.y;
+                if (cx) { dA[0][bb] += (float(cx) * wi) * duA; dB[0][bb] += (float(cx) * wi) * duB; }
+                if (cy) { dA[1][bb] += (float(cy) * wi) * duA; dB[1][bb] += (float(cy) * wi) * duB; }
+                if (cz) { dA[2][bb] += (float(cz) * wi) * duA; dB[2][bb] += (float(cz) * wi) * duB; }
+            }
+        }
+    }
+    FloatNode<Q, kUnits, CONTRAST> nA, nB;
+    nA.compute(P, NA, ph.x, gA, lA, dA);
+    nB.compute(P, NB, ph.y, gB, lB, dB);
+
+    // u and p of the pair in one store per field; 0 at a node that is not fluid
+    // (the velocity halo reads 0 at solid nodes)
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+        *reinterpret_cast<float2*>(b.u_out + a * pl + nodeA) =
+            make_float2(fluidA ? nA.u[a] : 0.f, fluidB ? nB.u[a] : 0.f);
+    *reinterpret_cast<float2*>(b.p + nodeA) = make_float2(fluidA ? nA.p : 0.f, fluidB ? nB.p : 0.f);
+    if ((fluidA && !(nA.uu < 1e30f)) || (fluidB && !(nB.uu < 1e30f))) atomicOr(err, kErrNonFinite);
+
+    auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
+    auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
+    float sNA = 0.f, sNB = 0.f, sBA = 0.f, sBB = 0.f;       // moving populations as stored (FP16 storage)
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const int o = L::opp(i);
+        float niA, noA, biA, boA, niB, noB, biB, boB;
+        nA.dir(P, i, niA, noA, biA, boA);
+        nB.dir(P, i, niB, noB, biB, boB);
+        PS::store_units2(Nmov, (i - 1) * pl + nodeA, niA, niB, sNA, sNB);
+        PS::store_units2(Nmov, (o - 1) * pl + nodeA, noA, noB, sNA, sNB);
+        PS::store_units2(Bmov, (i - 1) * pl + nodeA, biA, biB, sBA, sBB);
+        PS::store_units2(Bmov, (o - 1) * pl + nodeA, boA, boB, sBA, sBB);
+    }
+    float2 rn, rb;
+    if constexpr (PS::kExact) {
+        const float n0A = nA.rest_N(P), n0B = nB.rest_N(P);
+        rn = make_float2(n0A, n0B);
+        rb = make_float2(nA.rest_B(P, n0A), nB.rest_B(P, n0B));
+    } else {
+        using FN = FloatNode<Q, kUnits, CONTRAST>;
+        rn = make_float2(FN::rest_N_from_sum(sNA), FN::rest_N_from_sum(sNB));
+        rb = make_float2(nA.rest_B_from_sum(sBA), nB.rest_B_from_sum(sBB));
+    }
+    *reinterpret_cast<float2*>(PS::rest(b.Nout) + nodeA) = rn;
+    *reinterpret_cast<float2*>(PS::rest(b.Bout) + nodeA) = rb;
+}
+
+}  // namespace lbmgpu

@@ -12,6 +12,7 @@
 
 #include "lbm_aux.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_kernels_pair.cuh"
 
 namespace lbmgpu {
 
@@ -27,6 +28,7 @@ struct StepConfig {
     double exp_eps;
     double eps;                    // -(4/W) cos(theta)
     int ghost_rule;                // lbm_ghost_rule
+    bool pair = false;             // float arithmetic: the two-node step kernel (k_step_pair)
 };
 
 struct StepPtrs {
@@ -42,6 +44,8 @@ struct StepPtrs {
     int* err;
     const CUtensorMap* tm_phi = nullptr;   // tiled maps of phi and of u_in for the halo copies, or none
     const CUtensorMap* tm_u = nullptr;
+    const CUtensorMap* tm2_phi = nullptr;  // the same with the two-node kernel's box
+    const CUtensorMap* tm2_u = nullptr;
 };
 
 template <typename T, typename S>
@@ -52,17 +56,22 @@ struct Launch {
     template <int Q>
     static dim3 step_block();
     template <int Q>
+    static dim3 pair_grid(const Dims& d);
+    template <int Q>
     static void step_q(const StepConfig& c, const StepPtrs& p, cudaStream_t s);
     static void step(const StepConfig& c, const StepPtrs& p, cudaStream_t s);
-    static void phi(const StepConfig& c, const void* Bst, const uint32_t* mask, void* phi, cudaStream_t s);
+    static void phi(const StepConfig& c, const void* Bst, const uint32_t* mask, void* phi, int* err, cudaStream_t s);
     static void ghost(int GK, int rule, int64_t ng, const int32_t* node, const int32_t* corner, const void* wt,
-                      double exp_eps, double eps, void* phi, cudaStream_t s);
+                      double exp_eps, double eps, void* phi, int64_t plane, int* err, cudaStream_t s);
     static unsigned flat_blocks(const Dims& d);
     static void init_phi(const StepConfig& c, const uint8_t* cls, void* phi, int mode, const double ctr[3], double R0,
                          double ghost_value, cudaStream_t s);
     static void init_pops(const StepConfig& c, const uint8_t* cls, const void* phi, void* N, void* B, cudaStream_t s);
     static void build_mask(const StepConfig& c, const uint8_t* cls, uint32_t* mask, cudaStream_t s);
-    // base subtracted from direction i of N (is_b = false) or B (true) in storage
+    // base subtracted from direction i of N (is_b = false) or B (true) in
+    // storage; scatter_dir takes and gather_dir returns the values less this
+    // base (the host adds and subtracts it in double, so a float domain's
+    // state crosses the ABI with the precision of its stored deviations)
     static double storage_base(const StepConfig& c, int i, bool is_b);
     static void scatter_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* post_i,
                             const void* post_opp, void* st, cudaStream_t s);
@@ -84,7 +93,7 @@ struct Launch {
     static void ghost_batched(int GK, const void* tabs, const int64_t* begin, int ndom, int64_t total, cudaStream_t s);
     static size_t ghost_table_size() { return sizeof(GhostTable<T>); }
     static void fill_ghost_table(void* out, int64_t n, const int32_t* node, const int32_t* corner, const void* wt,
-                                 double exp_eps, double eps, void* phi, int rule);
+                                 double exp_eps, double eps, void* phi, int rule, int64_t plane, int* err);
     static int diag_blocks(const Dims& d);
     static void diag(const StepConfig& c, const uint8_t* cls, const void* Nst, const void* phi, const void* u,
                      const void* p, const ProbeDev& pr, double* partial, double* out, cudaStream_t s);

@@ -41,6 +41,12 @@ StepParams<T> Launch<T, S>::params(const StepConfig& c) {
     if (sizeof(T) == 4) chi_for_float(c.chi, chi);
     else std::memcpy(chi, c.chi, sizeof(chi));
     for (int i = 0; i < 19; ++i) P.chi[i] = (T)chi[i];
+    // exact chi minus the stored reference, by class: rest, axis (direction 1),
+    // diagonal/edge (direction 5 of D2Q9, 7 of D3Q19); zero in FP64
+    const int diag = c.Q == 9 ? 5 : 7;
+    P.chi_err[0] = (T)(c.chi[0] - chi[0]);
+    P.chi_err[1] = (T)(c.chi[1] - chi[1]);
+    P.chi_err[2] = (T)(c.chi[diag] - chi[diag]);
     P.c2chi = (T)c.c2chi;
     P.exp_eps = (T)c.exp_eps;
     return P;
@@ -62,6 +68,13 @@ dim3 Launch<T, S>::step_block() {
 
 template <typename T, typename S>
 template <int Q>
+dim3 Launch<T, S>::pair_grid(const Dims& d) {
+    using Tl = PairTile<Q>;
+    return dim3((d.nx + Tl::TX - 1) / Tl::TX, (d.ny + Tl::TY - 1) / Tl::TY, (d.nz + Tl::TZ - 1) / Tl::TZ);
+}
+
+template <typename T, typename S>
+template <int Q>
 void Launch<T, S>::step_q(const StepConfig& c, const StepPtrs& p, cudaStream_t s) {
     const StepParams<T> P = params(c);
     StepBuffers<T, S> b;
@@ -70,6 +83,22 @@ void Launch<T, S>::step_q(const StepConfig& c, const StepPtrs& p, cudaStream_t s
     b.mask = p.mask; b.err = p.err;
     CUtensorMap tm_phi{}, tm_u{};
     int tma = 0;
+    if constexpr (sizeof(T) == 4) {
+        if (c.pair) {
+            using Tl = PairTile<Q>;
+            if (p.tm2_phi && p.tm2_u) {
+                tm_phi = *p.tm2_phi;
+                tm_u = *p.tm2_u;
+                tma = 1;
+            }
+            const dim3 block(Tl::BX, Tl::TY, Tl::TZ);
+            if (c.contrast)
+                k_step_pair<Q, S, true><<<pair_grid<Q>(c.d), block, 0, s>>>(P, b, tm_phi, tm_u, tma);
+            else
+                k_step_pair<Q, S, false><<<pair_grid<Q>(c.d), block, 0, s>>>(P, b, tm_phi, tm_u, tma);
+            return;
+        }
+    }
     if (sizeof(T) == 4 && p.tm_phi && p.tm_u) {
         tm_phi = *p.tm_phi;
         tm_u = *p.tm_u;
@@ -87,24 +116,26 @@ void Launch<T, S>::step(const StepConfig& c, const StepPtrs& p, cudaStream_t s) 
 }
 
 template <typename T, typename S>
-void Launch<T, S>::phi(const StepConfig& c, const void* Bst, const uint32_t* mask, void* phi, cudaStream_t s) {
+void Launch<T, S>::phi(const StepConfig& c, const void* Bst, const uint32_t* mask, void* phi, int* err,
+                       cudaStream_t s) {
     const StepParams<T> P = params(c);
     if (c.Q == 9)
-        k_phi<9, T, S><<<step_grid<9>(c.d), step_block<9>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi);
+        k_phi<9, T, S><<<step_grid<9>(c.d), step_block<9>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi, err);
     else
-        k_phi<19, T, S><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi);
+        k_phi<19, T, S><<<step_grid<19>(c.d), step_block<19>(), 0, s>>>(P, (const S*)Bst, mask, (T*)phi, err);
 }
 
 template <typename T, typename S>
 void Launch<T, S>::ghost(int GK, int rule, int64_t ng, const int32_t* node, const int32_t* corner, const void* wt,
-                  double exp_eps, double eps, void* phi, cudaStream_t s) {
+                  double exp_eps, double eps, void* phi, int64_t plane, int* err, cudaStream_t s) {
     if (ng == 0) return;
     const unsigned blocks = (unsigned)((ng + 255) / 256);
     const T* w = (const T*)wt;
-    if (GK == 4 && rule == 0) k_ghost<4, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
-    if (GK == 4 && rule == 1) k_ghost<4, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
-    if (GK == 8 && rule == 0) k_ghost<8, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
-    if (GK == 8 && rule == 1) k_ghost<8, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, (T*)phi);
+    T* f = (T*)phi;
+    if (GK == 4 && rule == 0) k_ghost<4, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, f, plane, err);
+    if (GK == 4 && rule == 1) k_ghost<4, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, f, plane, err);
+    if (GK == 8 && rule == 0) k_ghost<8, T, 0><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, f, plane, err);
+    if (GK == 8 && rule == 1) k_ghost<8, T, 1><<<blocks, 256, 0, s>>>(ng, node, corner, w, (T)exp_eps, (T)eps, f, plane, err);
 }
 
 template <typename T, typename S>
@@ -155,7 +186,8 @@ double Launch<T, S>::storage_base(const StepConfig& c, int i, bool is_b) {
 template <typename T, typename S>
 void Launch<T, S>::scatter_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* post_i,
                         const void* post_opp, void* st, cudaStream_t s) {
-    const T base = (T)storage_base(c, i, is_b);
+    // the host subtracted storage_base in double: the values arrive as what is stored
+    const T base = T(0);
     const float scale = is_b ? kScaleB : kScaleN;
     if (c.Q == 9)
         k_scatter_dir<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const T*)post_i,
@@ -168,7 +200,8 @@ void Launch<T, S>::scatter_dir(const StepConfig& c, const uint8_t* cls, int i, b
 template <typename T, typename S>
 void Launch<T, S>::gather_dir(const StepConfig& c, const uint8_t* cls, int i, bool is_b, const void* st, void* post,
                        cudaStream_t s) {
-    const T base = (T)storage_base(c, i, is_b);
+    // the stored values as they are; the host adds storage_base in double
+    const T base = T(0);
     const float scale = is_b ? kScaleB : kScaleN;
     if (c.Q == 9)
         k_gather_dir<9, T, S><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, i, (const S*)st, base, scale, (T*)post);
@@ -242,10 +275,10 @@ void Launch<T, S>::ghost_batched(int GK, const void* tabs, const int64_t* begin,
 
 template <typename T, typename S>
 void Launch<T, S>::fill_ghost_table(void* out, int64_t n, const int32_t* node, const int32_t* corner, const void* wt,
-                             double exp_eps, double eps, void* phi, int rule) {
+                             double exp_eps, double eps, void* phi, int rule, int64_t plane, int* err) {
     GhostTable<T> g;
     g.n = n; g.node = node; g.corner = corner; g.wt = (const T*)wt; g.exp_eps = (T)exp_eps; g.eps = (T)eps;
-    g.phi = (T*)phi; g.rule = rule;
+    g.phi = (T*)phi; g.rule = rule; g.plane = plane; g.err = err;
     std::memcpy(out, &g, sizeof(g));
 }
 

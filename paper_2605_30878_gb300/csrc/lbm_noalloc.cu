@@ -54,8 +54,8 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_partial(const uint8_t* _
         acc[0] += 1.0;
         acc[1] += ph;
         acc[2] += 1.0 - ph;
-        if (u2 > acc[3]) acc[3] = u2;
-        if (!(u2 == u2) || !(ph == ph)) acc[4] += 1.0;
+        if (isfinite(u2) && u2 > acc[3]) acc[3] = u2;
+        if (!isfinite(u2) || !isfinite(ph)) acc[4] += 1.0;      // NaN or +-Inf in phi or u
     }
     __shared__ double s_w[NA_THREADS / 32][NA_REC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

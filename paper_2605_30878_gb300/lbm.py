@@ -11,12 +11,18 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+# LBM_LIBRARY=debug selects the bounds-checked build of the same sources
+# (liblbm_debug.so: every index the kernels compute is range-checked, a bad
+# one is reported as LBM_ERR_BOUNDS and its access skipped); anything else the
+# production library.
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm_debug.so" if os.environ.get("LBM_LIBRARY") == "debug"
+                        else "liblbm.so")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSTABLE, LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6
+LBM_ERR_BOUNDS = -7
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_UNSTABLE",
-                -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_UNSUPPORTED"}
+                -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_UNSUPPORTED", -7: "LBM_ERR_BOUNDS"}
 FP64, FP32, FP16 = 0, 1, 2     # FP16: FP32 arithmetic, FP16 population storage
 BATCH_TILE_SHAPES = 5          # LBM_BATCH_TILE_SHAPES: tile shapes / block sizes of the batched kernels
 GHOST_PRESENT, GHOST_FAKHARI = 0, 1
@@ -26,7 +32,8 @@ FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 EXPORTS = ("lbm_domain_bytes", "lbm_create_domain", "lbm_init_droplet", "lbm_init_phi", "lbm_step", "lbm_sync",
            "lbm_diagnostics", "lbm_read_state", "lbm_write_state", "lbm_profile_steps", "lbm_ghost_table", "lbm_ghost_fallbacks",
            "lbm_launches_per_step", "lbm_bytes_per_fluid_node", "lbm_fluid_nodes", "lbm_last_error", "lbm_destroy",
-           "lbm_phase_sums_noalloc", "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_tune",
+           "lbm_phase_sums_noalloc", "lbm_debug_expire_halo_wait", "lbm_debug_bounds_checked",
+           "lbm_debug_plant_bad_index", "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_tune",
            "lbm_batch_variant", "lbm_batch_set_variant", "lbm_batch_launches_per_step", "lbm_batch_last_error",
            "lbm_batch_destroy")
 
@@ -115,6 +122,12 @@ def load():
                                          C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_char_p,
                                          C.c_size_t]
     L.lbm_phase_sums_noalloc.restype = C.c_int
+    L.lbm_debug_expire_halo_wait.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
+    L.lbm_debug_expire_halo_wait.restype = C.c_int
+    L.lbm_debug_bounds_checked.argtypes = []
+    L.lbm_debug_bounds_checked.restype = C.c_int32
+    L.lbm_debug_plant_bad_index.argtypes = [C.c_void_p, C.c_int32]
+    L.lbm_debug_plant_bad_index.restype = C.c_int
     L.lbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]
     L.lbm_batch_create.restype = C.c_int
     L.lbm_batch_step.argtypes = [C.c_void_p, C.c_int64]
@@ -159,6 +172,11 @@ def make_probe(kind=0, center=(0, 0, 0), radius=0.0, normal=(0, 0, 0), exclude=0
     pr.normal[:] = [float(v) for v in (list(normal) + [0.0] * 3)[:3]]
     pr.exclude = float(exclude)
     return pr
+
+
+def bounds_checked():
+    """True when the loaded library is the bounds-checked build."""
+    return bool(load().lbm_debug_bounds_checked())
 
 
 def domain_bytes(params, n_ghosts):
@@ -336,6 +354,19 @@ class Domain:
         _check(load().lbm_ghost_table(self.h, cor.ctypes.data_as(C.POINTER(C.c_int64)), wt.ctypes.data_as(_dp),
                                       nc.ctypes.data_as(C.POINTER(C.c_int32))), self.h)
         return cor.reshape(n, GK)[:self.n_ghosts], wt.reshape(n, GK)[:self.n_ghosts], nc[:self.n_ghosts]
+
+    def debug_expire_halo_wait(self, timeout_ns, measure=False):
+        """Make one block's bounded halo-copy wait run out on the domain stream
+        (no copy is issued); the next sync reports LBM_ERR_TIMEOUT.  With
+        measure=True, synchronises and returns the measured wait in ns."""
+        w = C.c_int64(-1)
+        _check(load().lbm_debug_expire_halo_wait(self.h, int(timeout_ns), C.byref(w) if measure else None), self.h)
+        return w.value if measure else None
+
+    def debug_plant_bad_index(self, which=0):
+        """Bounds-checked library only: make the next step meet an index its
+        checks must catch (see lbm_debug_plant_bad_index)."""
+        _check(load().lbm_debug_plant_bad_index(self.h, int(which)), self.h)
 
     def ghost_fallbacks(self):
         return load().lbm_ghost_fallbacks(self.h)

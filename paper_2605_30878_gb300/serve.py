@@ -114,6 +114,7 @@ class GpuBackend:
         self.keep_final = keep_final                     # keep each case's final color field (tests)
         self.final = {}
         self.streams = {9: torch.cuda.Stream(), 19: torch.cuda.Stream()}
+        self._handles = {}                               # id(domain) -> handle
 
     def prepare(self, req):
         case = request_case(req, precision=self.precision)
@@ -129,7 +130,9 @@ class GpuBackend:
         probe = self.lbm.make_probe(1, case["solid_center"], case["R"], case["normal"],
                                     min(self.exclude, 0.5 * case["cap_height"]))
         case["solid"] = case["ghosts"] = None           # host copies are no longer needed
-        return dict(domain=d, probe=probe, rid=req.rid)
+        h = dict(domain=d, probe=probe, rid=req.rid)
+        self._handles[id(d)] = h
+        return h
 
     def batch(self, lattice, handles):
         if not self.batched:
@@ -149,12 +152,31 @@ class GpuBackend:
                     d.step(n)
 
     def wait(self, batches):
+        """Wait for the chunk; returns the handles of the cases whose device
+        state failed in it (a non-finite value, LBM_ERR_UNSTABLE, or a halo
+        copy that timed out, LBM_ERR_TIMEOUT).  The other cases go on."""
+        lbm = self.lbm
+        bad = []
         for b in batches:
-            if self.batched:
-                b.sync()
-            else:
-                for d in b:
+            doms = b.domains if self.batched else b
+            try:
+                if self.batched:
+                    b.sync()
+                else:
+                    for d in doms:
+                        d.sync()
+                continue
+            except lbm.LbmError as e:
+                if e.status not in (lbm.LBM_ERR_UNSTABLE, lbm.LBM_ERR_TIMEOUT):
+                    raise
+            for d in doms:                               # the batch names only its first failure
+                try:
                     d.sync()
+                except lbm.LbmError as e:
+                    if e.status not in (lbm.LBM_ERR_UNSTABLE, lbm.LBM_ERR_TIMEOUT):
+                        raise
+                    bad.append(self._handles[id(d)])
+        return bad
 
     def angle_deg(self, h):
         """Contact angle in degrees; NaN when no interface could be fitted, None
@@ -166,7 +188,8 @@ class GpuBackend:
 
     def close(self, h):
         if self.keep_final:
-            self.final[h["rid"]] = h["domain"].read("phi")
+            self.final[h["rid"]] = {f: h["domain"].read(f) for f in ("N", "B", "phi", "u", "p")}
+        self._handles.pop(id(h["domain"]), None)
         h["domain"].close()
 
 
@@ -186,6 +209,7 @@ class Result:
     theta_set: float = float("nan")
     theta_measured: float = float("nan")
     fluid_nodes: int = 0
+    error: str = ""
 
     @property
     def latency(self):
@@ -226,11 +250,19 @@ class Server:
             phase[name] += self.clock() - t1
             return out
 
+        def give_up(q, exc):
+            """A request whose set-up failed is retired as failed; the others go on."""
+            r = results[q.rid]
+            r.failed, r.finished, r.error = True, now(), "%s: %s" % (type(exc).__name__, exc)
+
         def arrivals():
             t = now()
             while pending and pending[0].arrival <= t:
                 q = pending.popleft()
-                waiting.append((q, timed("prepare", be.prepare, q)))
+                try:
+                    waiting.append((q, timed("prepare", be.prepare, q)))
+                except Exception as exc:                     # noqa: BLE001 -- reported in the result
+                    give_up(q, exc)
 
         while pending or waiting or active[9] or active[19]:
             arrivals()
@@ -243,7 +275,11 @@ class Server:
                 if used_bytes + case["bytes"] > self.memory_budget or n_act >= self.max_active:
                     break
                 waiting.popleft()
-                h = timed("open", be.open, q, case)
+                try:
+                    h = timed("open", be.open, q, case)
+                except Exception as exc:                     # noqa: BLE001 -- e.g. LBM_ERR_OOM
+                    give_up(q, exc)
+                    continue
                 used_bytes += case["bytes"]
                 active[q.lattice].append(dict(req=q, h=h, bytes=case["bytes"], steps=0, prev=None,
                                               fluid=case["fluid_nodes"]))
@@ -266,14 +302,17 @@ class Server:
             running = [batches[lat] for lat in (9, 19) if lat in batches]
             timed("launch", be.launch, running, self.chunk)
             arrivals()                                    # host-side set-up overlaps the chunk
-            timed("wait", be.wait, running)
+            broken = {id(h) for h in (timed("wait", be.wait, running) or ())}
             for lat in (9, 19):
                 keep = []
                 for e in active[lat]:
                     e["steps"] += self.chunk
                     node_steps += e["fluid"] * self.chunk
                     done = False
-                    if e["steps"] % self.check_every == 0:
+                    if id(e["h"]) in broken:                   # device state failed in this chunk
+                        r = results[e["req"].rid]
+                        done, r.failed, r.error = True, True, "device state failed"
+                    elif e["steps"] % self.check_every == 0:
                         th = timed("check", be.angle_deg, e["h"])
                         r = results[e["req"].rid]
                         if th is None:                           # non-finite state: the case failed

@@ -293,7 +293,7 @@ def packing_domain(centers, radii, n=256):
     def fn(x, y, z):
         pts = np.stack([x, y, z], axis=1)
         k = min(8, len(radii))
-        _, idx = tree.query(pts, k=k)
+        _, idx = tree.query(pts, k=k, workers=-1)       # each point's answer is independent of the split
         idx = idx.reshape(len(pts), k)
         best = np.full(len(pts), np.inf)
         out = np.zeros((len(pts), 3))

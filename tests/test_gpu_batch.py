@@ -1,14 +1,22 @@
 """Batched launches (many uneven domains, one launch per phase, one block per
-tile) against the same domains stepped one by one: identical to the bit, for
-every tile shape the autotuner can pick, for both lattices and every storage
-precision."""
+tile): every domain of a mixed batch against the FP64 oracle stepped alone,
+and against the same domains stepped one by one on the GPU (identical to the
+bit), for every tile shape the autotuner can pick, for both lattices and every
+storage precision."""
 import gc
+import math
+import os
+import sys
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2605_30878_gb300 import lbm
 from paper_2605_30878_gb300 import workloads as wl
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+import parity_util as pu  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +53,71 @@ def _make(cfgs):
         d.init_droplet(c["drop_center"], c["R0"])
         doms.append(d)
     return doms
+
+
+def _mixed_2d(precision, seed=13, count=5):
+    """D2Q9 drops on cylinders of different sizes, density ratios 1, 10, 1000
+    (viscosity ratio 100 at 1000, else 1) and both ghost rules."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        nx, ny = int(rng.integers(40, 120)), int(rng.integers(30, 80))
+        R = float(rng.uniform(0.1, 0.2) * min(nx, ny))
+        cfg = wl.cylinder_config(nx=nx, ny=ny, R=R, R0=0.8 * R, theta_deg=float(rng.uniform(20, 160)))
+        ratio = [1.0, 10.0, 1000.0][k % 3]
+        cfg["params"].update(precision=precision, ghost_rule=k % 2, rho_l=ratio, rho_g=1.0,
+                             mu_l=0.1 * (100.0 if ratio == 1000.0 else 1.0), mu_g=0.1)
+        out.append(cfg)
+    return out
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+@pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
+def test_mixed_batch_matches_the_oracle(precision, Q):
+    """Every domain of a mixed batch -- sizes, density ratios 1/10/1000, both
+    ghost rules, domains joining at both step parities -- against the FP64
+    oracle stepped alone from the same initial state: after 1 batched step
+    (tile shape 0, TMA halo on interior tiles) and after 9 more (tile shape 2,
+    element-copied halo), within the parity bounds of every precision."""
+    cfgs = _cases(precision, seed=13) if Q == 19 else _mixed_2d(precision)
+    doms = _make(cfgs)
+    orcs = []
+    for c in cfgs:
+        o = oracle.Oracle(c["params"], c["solid"], c["ghosts"])
+        o.init_droplet(c["drop_center"], c["R0"])
+        orcs.append(o)
+    early = (1, 3)                                   # these join the batch one step ahead (odd parity)
+    for k in early:
+        doms[k].step(1)
+        orcs[k].step(1)
+    b = lbm.Batch(doms)
+    taken = [1 + (k in early) for k in range(len(cfgs))]
+    for variant, n in ((0, 1), (2, 9)):
+        b.set_variant(variant)
+        b.step(n)
+        b.sync()
+        for k, (d, o, c) in enumerate(zip(doms, orcs, cfgs)):
+            o.step(n)
+            fluid = c["solid"].reshape(-1) == 0
+            steps = taken[k] + (n if variant == 2 else 0)
+            pu.check(pu.read_gpu(d), pu.read_oracle(o), c["params"], precision, fluid, steps,
+                     "batch Q=%d domain %d (ratio %g, rule %d) after %d steps" %
+                     (Q, k, c["params"]["rho_l"], c["params"].get("ghost_rule", 0), steps))
+    # the batched step map itself: each oracle takes its domain's GPU state,
+    # the batch and the oracles advance one step from identical inputs
+    fresh = []
+    for d, c in zip(doms, cfgs):
+        o = oracle.Oracle(c["params"], c["solid"], c["ghosts"])
+        for f in ("N", "B", "phi", "u", "p"):
+            o.set(f, d.read(f))
+        fresh.append(o)
+    b.step(1)
+    b.sync()
+    for k, (d, o, c) in enumerate(zip(doms, fresh, cfgs)):
+        o.step(1)
+        pu.check(pu.read_gpu(d), pu.read_oracle(o), c["params"], precision, c["solid"].reshape(-1) == 0, 1,
+                 "batch Q=%d domain %d, one step from its GPU state" % (Q, k))
+    b.close()
 
 
 @pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32, lbm.FP16])
@@ -175,25 +248,31 @@ def test_batch_size_limit():
 
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16])
 @pytest.mark.parametrize("Q", [9, 19])
-def test_tma_halo_equals_element_copies(precision, Q):
+def test_tma_halo_equals_element_copies(precision, Q, monkeypatch):
     """Large enough for tiles whose halo needs no periodic image in y, z: the
     single-domain step kernel copies their halo with tiled TMA loads from
-    kernel-parameter maps, the batched kernel with tile shape 0 from maps in
-    global memory, and with tile shape 1 element by element; the three states
-    must agree to the bit."""
+    kernel-parameter maps, the batched kernel with every tile shape from maps
+    in global memory; a domain created with LBM_HALO_COPY=elements copies
+    every halo element by element.  All states must agree to the bit."""
     if Q == 19:
         cfg = wl.sphere_config(n=96, R=20.0, R0=14.0, theta_deg=70.0, rho_ratio=1000.0, precision=precision)
     else:
         cfg = wl.cylinder_config(nx=160, ny=128, R=20.0, R0=16.0, theta_deg=110.0)
         cfg["params"].update(precision=precision, rho_l=1000.0, rho_g=1.0, mu_l=10.0, mu_g=0.1)
-    alone, mixed, copied = _make([cfg]), _make([cfg]), _make([cfg])
-    alone[0].step(9)
-    for doms, variant in ((mixed, 0), (copied, 1)):
+    monkeypatch.setenv("LBM_HALO_COPY", "elements")
+    copied = _make([cfg])
+    monkeypatch.delenv("LBM_HALO_COPY")
+    alone = _make([cfg])
+    for d in copied + alone:
+        d.step(9)
+    want = {f: copied[0].read(f) for f in ("N", "B", "phi", "u", "p")}
+    for f in want:
+        assert np.array_equal(alone[0].read(f), want[f]), ("single domain, TMA", f)
+    for variant in range(lbm.BATCH_TILE_SHAPES):
+        doms = _make([cfg])
         with lbm.Batch(doms) as b:
             b.set_variant(variant)
             b.step(9)
             b.sync()
-    for f in ("N", "B", "phi", "u", "p"):
-        a = alone[0].read(f)
-        assert np.array_equal(a, mixed[0].read(f)), ("TMA, global maps", f)
-        assert np.array_equal(a, copied[0].read(f)), ("element copies", f)
+        for f in want:
+            assert np.array_equal(doms[0].read(f), want[f]), ("batched TMA, tile shape %d" % variant, f)

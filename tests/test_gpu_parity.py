@@ -1,13 +1,13 @@
 """GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
 
-Tolerances (relative L-infinity over fluid nodes, max|gpu - oracle| / max|oracle|):
-FP64 1e-12 and FP32 1e-4 on the populations N, B and on phi.  u and p are
-linear in the populations with O(1) coefficients (Eqs. velUpdate and
-pressureUpdate: p = 3 (sum_{i>0} N_i - (1-chi_0))/(1-w_0) - ...), and both are
-small differences of O(0.1) sums, so their error is the populations' error
-times O(1), not a fraction of their own small size: they are compared on the
-population scale, max(max|oracle|, 1), with the same bounds."""
+Populations N, B and phi: relative L-infinity error over fluid nodes,
+max|gpu - oracle| / max|oracle|, at most 1e-12 (FP64), 1e-4 (FP32) or 2e-3
+(FP16 population storage).  u and p on their own scale: at most that bound
+times max|oracle| plus the rounding budget of the sums that produce them
+(tests/parity_util.py states and derives it)."""
 import math
+import os
+import sys
 
 import numpy as np
 import pytest
@@ -16,13 +16,17 @@ import oracle
 from paper_2605_30878_gb300 import lbm
 from paper_2605_30878_gb300 import workloads as wl
 
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+import parity_util as pu  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 # FP16 storage keeps 11 significant bits of the stored deviations; a B
 # deviation reaches chi_0/2 ~ 0.46, so one stored value carries up to 2.2e-4 of
 # rounding (2.4e-4 relative to max B) and phi sums 19 of them: 2e-3 leaves room
 # for a few steps of accumulation.
-TOL = {lbm.FP64: 1e-12, lbm.FP32: 1e-4, lbm.FP16: 2e-3}
+TOL = pu.TOL
+rel = pu.rel
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,16 +39,6 @@ def _lib():
     lbm.load()
 
 
-FLOOR = {"N": 0.0, "B": 0.0, "phi": 0.0, "u": 1.0, "p": 1.0}
-
-
-def rel(a, b, mask=None, floor=0.0):
-    if mask is not None:
-        a, b = a[..., mask], b[..., mask]
-    den = max(np.abs(b).max(), floor)
-    return np.abs(a - b).max() / (den if den > 0 else 1.0)
-
-
 def pair(cfg, precision):
     P = dict(cfg["params"], precision=precision)
     g = lbm.Domain(P, cfg["solid"], cfg["ghosts"])
@@ -52,16 +46,10 @@ def pair(cfg, precision):
     return g, o
 
 
-def compare(g, o, solid, precision, what=("N", "B", "phi", "u", "p")):
-    fluid = solid.reshape(-1) == 0
-    out = {}
-    for f in what:
-        a, b = g.read(f), o.get(f)
-        out[f] = rel(a, b, fluid, FLOOR[f])
-    tol = TOL[precision]
-    bad = {k: v for k, v in out.items() if not v <= tol}
-    assert not bad, "relative L-inf above %g: %s" % (tol, bad)
-    return out
+def compare(g, o, cfg, precision, steps, label=""):
+    """Every field of the GPU state against the oracle's (see parity_util)."""
+    fluid = cfg["solid"].reshape(-1) == 0
+    return pu.check(pu.read_gpu(g), pu.read_oracle(o), cfg["params"], precision, fluid, steps, label)
 
 
 def small_3d(theta=60.0, rho_ratio=1000.0, shape=(28, 36, 40), R=7.0, R0=6.0):
@@ -100,7 +88,7 @@ def test_initial_state_matches(precision):
     g, o = pair(cfg, precision)
     g.init_droplet(cfg["drop_center"], cfg["R0"])
     o.init_droplet(cfg["drop_center"], cfg["R0"])
-    compare(g, o, cfg["solid"], precision)
+    compare(g, o, cfg, precision, 0, "initial state")
     # the ghost table is the same reading of Fig. 2 on both sides
     gc, gw, gn = g.ghost_table()
     oc, ow, on = o.ghost_table()
@@ -137,7 +125,7 @@ def test_one_step_from_a_random_state(Q, rho_ratio, precision):
         setter("N", N); setter("B", B); setter("u", u); setter("p", p); setter("phi", phi)
     g.step(1)
     o.step(1)
-    compare(g, o, cfg["solid"], precision)
+    compare(g, o, cfg, precision, 1, "random state, Q=%d ratio=%g" % (Q, rho_ratio))
 
 
 def _resync_one_step(g, cfg, precision):
@@ -148,7 +136,7 @@ def _resync_one_step(g, cfg, precision):
         o.set(f, g.read(f))
     g.step(1)
     o.step(1)
-    compare(g, o, cfg["solid"], precision)
+    compare(g, o, cfg, precision, 1, "resync at step %d" % g.diagnostics()["step"])
 
 
 @pytest.mark.parametrize("precision", [lbm.FP64, lbm.FP32])
@@ -214,7 +202,8 @@ def test_sphere_3d_parity_ragged_tiles(precision):
         g.step(target - done)
         o.step(target - done)
         done = target
-        compare(g, o, cfg["solid"], precision)
+        compare(g, o, cfg, precision, target, "sphere 40x36x28 step %d" % target)
+    _resync_one_step(g, cfg, precision)                # the step map from the evolved state
 
 
 @pytest.mark.parametrize("shape,Q", [((1, 3, 5), 9), ((3, 2, 5), 19), ((1, 1, 1), 9), ((2, 2, 2), 19)])
@@ -232,7 +221,7 @@ def test_tiny_and_solid_free_domains(shape, Q):
     o.init_phi(phi)
     g.step(3)
     o.step(3)
-    compare(g, o, solid, lbm.FP64)
+    compare(g, o, cfg, lbm.FP64, 3, "tiny %s" % (shape,))
     assert g.launches_per_step() == 2
 
 
@@ -262,7 +251,7 @@ def test_neutral_angle_and_flat_wall_fp64():
     o.init_droplet((20, 1, 0), 9)
     g.step(50)
     o.step(50)
-    compare(g, o, solid, lbm.FP64)
+    compare(g, o, cfg, lbm.FP64, 50, "flat walls, 90 deg")
 
 
 def test_mass_conservation_and_determinism_fp64():
@@ -348,7 +337,7 @@ def test_fakhari_rule_parity_fp64(theta_deg):
     o.init_droplet(cfg["drop_center"], cfg["R0"])
     g.step(300)
     o.step(300)
-    compare(g, o, cfg["solid"], lbm.FP64)
+    compare(g, o, cfg, lbm.FP64, 300, "Fakhari rule %g deg" % theta_deg)
     if theta_deg == 90.0:
         cor, wt, nc = o.ghost_table()
         phi = g.read("phi")
@@ -356,3 +345,42 @@ def test_fakhari_rule_parity_fp64(theta_deg):
         ghost_nodes = cfg["ghosts"][0]
         phiF = np.array([np.dot(wt[k, :nc[k]], phi[cor[k, :nc[k]]]) for k in range(len(ghost_nodes))])
         assert np.abs(g.read("phi")[ghost_nodes] - phiF).max() < 1e-14
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16])
+@pytest.mark.parametrize("Q", [9, 19])
+def test_two_node_kernel_equals_one_node_kernel(precision, Q, monkeypatch):
+    """The two-node step kernel (each thread updates x-adjacent nodes, two-wide
+    loads and stores) and the one-node kernel round alike: the same state to
+    the bit after 11 steps, on grids whose odd x extent leaves the last pair
+    half outside the grid, with tiled and element-copied halos."""
+    if Q == 19:
+        cfg = wl.sphere_config(n=70, R=14.0, R0=10.0, theta_deg=50.0, rho_ratio=1000.0, precision=precision)
+        shape = (67, 70, 69)                       # nz, ny, nx: odd nx
+        center = (34.3, 35.2, 33.6)
+        solid, ghosts = wl.sphere_domain(19, shape, center, 14.0)
+        cfg.update(solid=solid, ghosts=ghosts, drop_center=tuple(wl.droplet_on_sphere_center(
+            center, 14.0, 10.0, math.radians(50.0))))
+        cfg["params"].update(nx=69, ny=70, nz=67)
+    else:
+        cfg = wl.cylinder_config(nx=161, ny=130, R=20.0, R0=16.0, theta_deg=110.0)
+        cfg["params"].update(precision=precision, rho_l=1000.0, rho_g=1.0, mu_l=10.0, mu_g=0.1)
+    states = {}
+    for kernel in ("single", "pair"):
+        for halo in ("tma", "elements"):
+            monkeypatch.setenv("LBM_STEP_KERNEL", kernel)
+            if halo == "elements":
+                monkeypatch.setenv("LBM_HALO_COPY", "elements")
+            else:
+                monkeypatch.delenv("LBM_HALO_COPY", raising=False)
+            d = lbm.Domain(dict(cfg["params"], precision=precision), cfg["solid"], cfg["ghosts"])
+            monkeypatch.delenv("LBM_STEP_KERNEL")
+            monkeypatch.delenv("LBM_HALO_COPY", raising=False)
+            d.init_droplet(cfg["drop_center"], cfg["R0"])
+            d.step(11)
+            d.sync()
+            states[(kernel, halo)] = {f: d.read(f) for f in ("N", "B", "phi", "u", "p")}
+    ref = states[("single", "tma")]
+    for key, st in states.items():
+        for f in ref:
+            assert np.array_equal(st[f], ref[f]), (key, f)

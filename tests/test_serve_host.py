@@ -203,3 +203,65 @@ def test_batches_never_hold_more_slots_than_the_table():
     reqs = [serve.Request(i, 0.001 * i, 9 if i % 3 else 19, 24 + (i % 7), 60.0, 1.0) for i in range(40)]
     serve.Server(be, 10 ** 12, max_active=8, clock=clk, sleep=clk.sleep).run(reqs)
     assert Slots.peak <= 8 and Slots.live == 0
+
+
+class OomError(RuntimeError):
+    """Stands in for lbm.LbmError(LBM_ERR_OOM) from lbm_create_domain."""
+
+
+def test_allocation_failure_mid_stream_retires_only_that_request():
+    """Request 3's domain creation fails with an out-of-memory error while
+    others are running: it is retired as failed at once, the rest converge,
+    and the budget bookkeeping stays balanced (nothing was charged for it)."""
+    class FailingOpen(FakeBackend):
+        def open(self, req, case):
+            if req.rid == 3:
+                raise OomError("LBM_ERR_OOM: cudaMalloc of %d bytes failed" % case["bytes"])
+            return super().open(req, case)
+    clk = SimClock()
+    be = FailingOpen(clk)
+    reqs = [serve.Request(i, 0.002 * i, 9 if i % 2 else 19, 32 + i, 40.0 + 5 * i, 1.0) for i in range(7)]
+    res, summ = serve.Server(be, 10 ** 12, max_active=4, clock=clk, sleep=clk.sleep).run(reqs)
+    bad = res[3]
+    assert bad.failed and not bad.converged and bad.steps == 0
+    assert "OomError" in bad.error and "LBM_ERR_OOM" in bad.error
+    assert bad.finished >= bad.arrival and math.isnan(bad.admitted)
+    assert all(r.converged and not r.failed for k, r in enumerate(res) if k != 3)
+    assert summ["failed"] == 1 and summ["converged"] == 6
+    assert 3 not in be.opened and sorted(be.closed) == [0, 1, 2, 4, 5, 6]
+    assert be.live_bytes == 0
+    for lat, members in be.batches_made:
+        assert 3 not in members
+
+
+def test_device_failure_in_a_chunk_retires_that_case():
+    """The backend's wait reports one case's device state as failed (as the GPU
+    backend does for LBM_ERR_UNSTABLE or LBM_ERR_TIMEOUT): that case retires as
+    failed after the chunk, its batch is rebuilt without it, the others go on."""
+    class FailingDevice(FakeBackend):
+        def wait(self, batches):
+            super().wait(batches)
+            return [h for b in batches for h in b if h["req"].rid == 1 and h["steps"] >= 600]
+    clk = SimClock()
+    be = FailingDevice(clk)
+    reqs = [serve.Request(i, 0.0, 9, 40, 60.0, 1.0) for i in range(4)]
+    res, summ = serve.Server(be, 10 ** 12, clock=clk, sleep=clk.sleep).run(reqs)
+    assert res[1].failed and res[1].steps == 600 and res[1].error == "device state failed"
+    assert all(r.converged for k, r in enumerate(res) if k != 1)
+    assert sorted(be.closed) == [0, 1, 2, 3] and be.live_bytes == 0
+    later = [m for lat, m in be.batches_made[1:]]
+    assert later and all(1 not in m for m in later)
+
+
+def test_prepare_failure_is_a_failed_request():
+    class FailingPrepare(FakeBackend):
+        def prepare(self, req):
+            if req.rid == 0:
+                raise ValueError("bad geometry")
+            return super().prepare(req)
+    clk = SimClock()
+    be = FailingPrepare(clk)
+    reqs = [serve.Request(i, 0.0, 19, 24, 60.0, 1.0) for i in range(2)]
+    res, summ = serve.Server(be, 10 ** 12, clock=clk, sleep=clk.sleep).run(reqs)
+    assert res[0].failed and "bad geometry" in res[0].error and res[1].converged
+    assert be.opened == [1]
