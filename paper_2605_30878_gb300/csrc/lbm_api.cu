@@ -406,7 +406,8 @@ bool encode_halo_maps_any(const lbm_domain* d, int V, CUtensorMap out[3]) {
         case 1: return encode_halo_maps<9, 1>(d, out);
         case 2: return encode_halo_maps<9, 2>(d, out);
         case 3: return encode_halo_maps<9, 3>(d, out);
-        default: return encode_halo_maps<9, 4>(d, out);
+        case 4: return encode_halo_maps<9, 4>(d, out);
+        default: return encode_halo_maps<9, 5>(d, out);
         }
     }
     switch (V) {
@@ -414,7 +415,8 @@ bool encode_halo_maps_any(const lbm_domain* d, int V, CUtensorMap out[3]) {
     case 1: return encode_halo_maps<19, 1>(d, out);
     case 2: return encode_halo_maps<19, 2>(d, out);
     case 3: return encode_halo_maps<19, 3>(d, out);
-    default: return encode_halo_maps<19, 4>(d, out);
+    case 4: return encode_halo_maps<19, 4>(d, out);
+    default: return encode_halo_maps<19, 5>(d, out);
     }
 }
 
@@ -573,10 +575,15 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     c.eps = -(4.0 / P.W) * std::cos(P.theta);
     c.exp_eps = std::exp(c.eps);
     c.ghost_rule = P.ghost_rule;
-    // float arithmetic: the one-node step kernel, or the two-node kernel with
-    // LBM_STEP_KERNEL=pair (both give the same results to the bit)
+    // Float arithmetic: the two-node step kernel with FP32 storage (memory-bound:
+    // half the load/store and address instructions per node raise its
+    // bandwidth, 0.89 -> 0.96 of the measured copy peak at 192^3), the one-node
+    // kernel with FP16 storage (issue-bound: the two-node kernel's halved
+    // occupancy made it 4% slower there).  LBM_STEP_KERNEL=pair|single
+    // overrides; both give the same results to the bit.
     const char* step_kernel = std::getenv("LBM_STEP_KERNEL");
-    c.pair = P.precision != LBM_FP64 && step_kernel && std::strcmp(step_kernel, "pair") == 0;
+    c.pair = P.precision != LBM_FP64 && (step_kernel ? std::strcmp(step_kernel, "pair") == 0
+                                                     : P.precision == LBM_FP32);
 
     // node classes: a solid node with a fluid stencil neighbour is a ghost
     const int64_t nn = L.nn_dense;

@@ -184,15 +184,18 @@ struct StepBuffers {
 // so the pull in direction i bounces back; MASK_NOT_FLUID marks non-fluid x.
 constexpr uint32_t MASK_NOT_FLUID = 0x80000000u;
 
-// Block tiles of the step kernels, one node per thread, in the shapes the
-// batch autotuner chooses between (V = 0 is the single-domain kernels' tile):
-//   V        0        1        2        3        4
-//   D3Q19  32x4x2   32x2x4   32x8x1   32x2x2   32x4x4
-//   D2Q9   32x8     64x4     128x2    32x4     32x16
-//   threads  256      256      256      128      512
-constexpr int kTileVariants = 5;
+// Block tiles of the step kernels in the shapes the batch autotuner chooses
+// between (V = 0 is the one-node single-domain kernel's tile), in nodes:
+//   V        0        1        2        3        4        5
+//   D3Q19  32x4x2   32x2x4   32x8x1   32x2x2   32x4x4   64x2x2
+//   D2Q9   32x8     64x4     128x2    32x4     32x16    64x4
+//   threads  256      256      256      128      512    128 (float: two nodes each), 256 (FP64)
+// Shape 5 is the tile of the two-node kernel (k_step_pair, PairTile); FP64
+// steps it one node per thread.
+constexpr int kTileVariants = 6;
 __host__ __device__ constexpr int tile_extent(int Q, int V, int axis) {
-    return Q == 9 ? (axis == 0 ? (V == 1 ? 64 : (V == 2 ? 128 : 32))
+    return V == 5 ? (axis == 0 ? 64 : axis == 1 ? (Q == 9 ? 4 : 2) : (Q == 9 ? 1 : 2))
+         : Q == 9 ? (axis == 0 ? (V == 1 ? 64 : (V == 2 ? 128 : 32))
                                : axis == 1 ? (V == 0 ? 8 : (V == 1 ? 4 : (V == 2 ? 2 : (V == 3 ? 4 : 16)))) : 1)
                   : (axis == 0 ? 32
                                : axis == 1 ? (V == 0 ? 4 : (V == 1 ? 2 : (V == 2 ? 8 : (V == 3 ? 2 : 4))))

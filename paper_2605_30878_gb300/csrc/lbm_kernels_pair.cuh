@@ -56,31 +56,24 @@ __device__ __forceinline__ float2 halo_pair(const float* s, int hc, int o, int* 
     return make_float2(lo.y, hi.x);
 }
 
+// The pair tile at (x0, y0, z0); maps != nullptr: tiled halo copies (the
+// caller checked the tile needs no periodic image in y and z and initialised
+// the barrier).
 template <int Q, typename S, bool CONTRAST>
-__global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
-    k_step_pair(StepParams<float> P, StepBuffers<float, S> b, const __grid_constant__ CUtensorMap tm_phi,
-                const __grid_constant__ CUtensorMap tm_u, int tma) {
+__device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const StepBuffers<float, S>& b,
+                                               float* s_phi, float* s_u, int x0, int y0, int z0,
+                                               const CUtensorMap* tm_phi, const CUtensorMap* tm_u,
+                                               uint64_t* bar) {
     using Tl = PairTile<Q>;
     using L = Lattice<Q>;
     using PS = PopStore<S>;
     constexpr int D = L::D;
     constexpr bool kUnits = !PS::kExact;
-    __shared__ __align__(128) float s_phi[Tl::HN];
-    __shared__ __align__(128) float s_u[CONTRAST ? D * Tl::HN : 2];
-    __shared__ __align__(8) uint64_t s_bar;
     int* const err = b.err;
-    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
-    // tiles whose halo needs no periodic image in y and z (x images are patched)
-    const bool interior = tma && y0 >= 1 && y0 + Tl::TY + 1 <= P.ny &&
-                          (D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= P.nz));
-    if (interior) {
-        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
-        __syncthreads();                                      // the barrier exists before anyone waits on it
-    }
+    const bool interior = tm_phi != nullptr;
     float fix_v;
     int fix_at;
-    if (!halo_issue<Tl, float, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, interior ? &tm_phi : nullptr, &tm_u,
-                                            &s_bar, fix_v, fix_at))
+    if (!halo_issue<Tl, float, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, tm_phi, tm_u, bar, fix_v, fix_at))
         return;
 
     // the pair's populations, pulled while the halo is in flight
@@ -129,7 +122,7 @@ __global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
                     NB[i] = (float)PS::load_units(mv, idx_checked((L::opp(i) - 1) * pl + nodeA + 1, nmv, err));
         }
     }
-    const bool halo_ok = halo_complete<Tl, float, S>(b, interior, &s_bar, s_phi, s_u, fix_v, fix_at);
+    const bool halo_ok = halo_complete<Tl, float, S>(b, interior, bar, s_phi, s_u, fix_v, fix_at);
     __syncthreads();
     if (!(fluidA || fluidB) || !halo_ok) return;
 
@@ -205,6 +198,52 @@ __global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
     }
     *reinterpret_cast<float2*>(PS::rest(b.Nout) + nodeA) = rn;
     *reinterpret_cast<float2*>(PS::rest(b.Bout) + nodeA) = rb;
+}
+
+template <int Q, typename S, bool CONTRAST>
+__global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
+    k_step_pair(StepParams<float> P, StepBuffers<float, S> b, const __grid_constant__ CUtensorMap tm_phi,
+                const __grid_constant__ CUtensorMap tm_u, int tma) {
+    using Tl = PairTile<Q>;
+    constexpr int D = Tl::D;
+    __shared__ __align__(128) float s_phi[Tl::HN];
+    __shared__ __align__(128) float s_u[CONTRAST ? D * Tl::HN : 2];
+    __shared__ __align__(8) uint64_t s_bar;
+    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::TZ;
+    // tiles whose halo needs no periodic image in y and z (x images are patched)
+    const bool interior = tma && y0 >= 1 && y0 + Tl::TY + 1 <= P.ny &&
+                          (D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= P.nz));
+    if (interior) {
+        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
+        __syncthreads();                                      // the barrier exists before anyone waits on it
+    }
+    step_pair_tile<Q, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, interior ? &tm_phi : nullptr, &tm_u, &s_bar);
+}
+
+// Batched form: one pair tile of one domain per block, the domain's
+// parameters in its constant-memory slot (as k_step_batched, tile shape 5).
+template <int Q, typename S, bool CONTRAST>
+__global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
+    k_step_pair_batched(const int4* __restrict__ tiles, const CUtensorMap* __restrict__ maps, int parity) {
+    using Tl = PairTile<Q>;
+    constexpr int D = Tl::D;
+    __shared__ __align__(128) float s_phi[Tl::HN];
+    __shared__ __align__(128) float s_u[CONTRAST ? D * Tl::HN : 2];
+    __shared__ __align__(8) uint64_t s_bar;
+    const int4 t = __ldg(tiles + blockIdx.x);          // {slot, x0, y0, z0}
+    const BatchEntry<float, S>& e = c_batch<float, S>[idx_checked(t.x, kBatchSlots, c_batch<float, S>[0].b[0].err)];
+    const int y0 = t.z, z0 = t.w;
+    if (kDebugBounds && !(idx_ok(t.y, e.P.nx, e.b[0].err) && idx_ok(y0, e.P.ny, e.b[0].err) &&
+                          idx_ok(z0, e.P.nz, e.b[0].err)))
+        return;                                         // a tile outside its domain
+    const bool tma = maps != nullptr && e.tma && y0 >= 1 && y0 + Tl::TY + 1 <= e.P.ny &&
+                     (D == 2 || (z0 >= 1 && z0 + Tl::TZ + 1 <= e.P.nz));
+    if (tma) {
+        if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
+        __syncthreads();                                      // the barrier exists before anyone waits on it
+    }
+    step_pair_tile<Q, S, CONTRAST>(e.P, e.b[parity], s_phi, s_u, t.y, y0, z0, tma ? maps + 3 * t.x : nullptr,
+                                   maps + 3 * t.x + 1 + parity, &s_bar);
 }
 
 }  // namespace lbmgpu

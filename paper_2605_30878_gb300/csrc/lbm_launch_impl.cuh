@@ -216,10 +216,22 @@ void Launch<T, S>::step_batched_v(const int4* tiles, const CUtensorMap* maps, in
                                   cudaStream_t s) {
     using Tl = Tile<Qc, V>;
     const dim3 block(Tl::TX, Tl::TY, Tl::TZ);     // the tile shape, as in the single-domain kernels
-    if (ncontrast > 0)
-        k_step_batched<Qc, T, S, V, true><<<ncontrast, block, 0, s>>>(tiles, maps, parity);
-    if (ntiles > ncontrast)
-        k_step_batched<Qc, T, S, V, false><<<ntiles - ncontrast, block, 0, s>>>(tiles + ncontrast, maps, parity);
+    if constexpr (V == 5 && sizeof(T) == 4) {
+        // float arithmetic: the two-node kernel over the same tiles, two nodes per thread
+        using Pt = PairTile<Qc>;
+        const dim3 pblock(Pt::BX, Pt::TY, Pt::TZ);
+        if (ncontrast > 0)
+            k_step_pair_batched<Qc, S, true><<<ncontrast, pblock, 0, s>>>(tiles, maps, parity);
+        if (ntiles > ncontrast)
+            k_step_pair_batched<Qc, S, false><<<ntiles - ncontrast, pblock, 0, s>>>(tiles + ncontrast, maps,
+                                                                                   parity);
+    } else {
+        if (ncontrast > 0)
+            k_step_batched<Qc, T, S, V, true><<<ncontrast, block, 0, s>>>(tiles, maps, parity);
+        if (ntiles > ncontrast)
+            k_step_batched<Qc, T, S, V, false><<<ntiles - ncontrast, block, 0, s>>>(tiles + ncontrast, maps,
+                                                                                    parity);
+    }
     k_phi_batched<Qc, T, S, V><<<ntiles, block, 0, s>>>(tiles, parity);
 }
 
@@ -236,12 +248,14 @@ void Launch<T, S>::step_phi_batched(int Q, int V, const int4* tiles, const CUten
         if (V == 2) step_batched_v<9, 2>(tiles, maps, ntiles, ncontrast, parity, s);
         if (V == 3) step_batched_v<9, 3>(tiles, maps, ntiles, ncontrast, parity, s);
         if (V == 4) step_batched_v<9, 4>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 5) step_batched_v<9, 5>(tiles, maps, ntiles, ncontrast, parity, s);
     } else {
         if (V == 0) step_batched_v<19, 0>(tiles, maps, ntiles, ncontrast, parity, s);
         if (V == 1) step_batched_v<19, 1>(tiles, maps, ntiles, ncontrast, parity, s);
         if (V == 2) step_batched_v<19, 2>(tiles, maps, ntiles, ncontrast, parity, s);
         if (V == 3) step_batched_v<19, 3>(tiles, maps, ntiles, ncontrast, parity, s);
         if (V == 4) step_batched_v<19, 4>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 5) step_batched_v<19, 5>(tiles, maps, ntiles, ncontrast, parity, s);
     }
 }
 

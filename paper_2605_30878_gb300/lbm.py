@@ -24,7 +24,7 @@ LBM_ERR_BOUNDS = -7
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_OOM", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_UNSTABLE",
                 -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_UNSUPPORTED", -7: "LBM_ERR_BOUNDS"}
 FP64, FP32, FP16 = 0, 1, 2     # FP16: FP32 arithmetic, FP16 population storage
-BATCH_TILE_SHAPES = 5          # LBM_BATCH_TILE_SHAPES: tile shapes / block sizes of the batched kernels
+BATCH_TILE_SHAPES = 6          # LBM_BATCH_TILE_SHAPES: tile shapes / block sizes of the batched kernels
 GHOST_PRESENT, GHOST_FAKHARI = 0, 1
 FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 

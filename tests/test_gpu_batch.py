@@ -76,9 +76,10 @@ def _mixed_2d(precision, seed=13, count=5):
 def test_mixed_batch_matches_the_oracle(precision, Q):
     """Every domain of a mixed batch -- sizes, density ratios 1/10/1000, both
     ghost rules, domains joining at both step parities -- against the FP64
-    oracle stepped alone from the same initial state: after 1 batched step
-    (tile shape 0, TMA halo on interior tiles) and after 9 more (tile shape 2,
-    element-copied halo), within the parity bounds of every precision."""
+    oracle stepped alone from the same initial state, after each of three legs
+    (tile shape 0 for 1 step, shape 5 -- two nodes per thread in float -- for
+    4, shape 2 for 5; TMA halos on interior tiles, element copies at the y and
+    z ends), within the parity bounds of every precision."""
     cfgs = _cases(precision, seed=13) if Q == 19 else _mixed_2d(precision)
     doms = _make(cfgs)
     orcs = []
@@ -91,15 +92,16 @@ def test_mixed_batch_matches_the_oracle(precision, Q):
         doms[k].step(1)
         orcs[k].step(1)
     b = lbm.Batch(doms)
-    taken = [1 + (k in early) for k in range(len(cfgs))]
-    for variant, n in ((0, 1), (2, 9)):
+    taken = [int(k in early) for k in range(len(cfgs))]
+    for variant, n in ((0, 1), (5, 4), (2, 5)):
         b.set_variant(variant)
         b.step(n)
         b.sync()
         for k, (d, o, c) in enumerate(zip(doms, orcs, cfgs)):
             o.step(n)
             fluid = c["solid"].reshape(-1) == 0
-            steps = taken[k] + (n if variant == 2 else 0)
+            taken[k] += n
+            steps = taken[k]
             pu.check(pu.read_gpu(d), pu.read_oracle(o), c["params"], precision, fluid, steps,
                      "batch Q=%d domain %d (ratio %g, rule %d) after %d steps" %
                      (Q, k, c["params"]["rho_l"], c["params"].get("ghost_rule", 0), steps))
@@ -129,7 +131,7 @@ def test_batch_equals_individual_steps(precision):
     mixed = _make(cfgs)
     mixed[1].step(1)                      # domains may enter the batch at different parities
     b = lbm.Batch(mixed)
-    for v, n in ((1, 5), (2, 4), (0, 3), (3, 2), (4, 2)):
+    for v, n in ((1, 5), (2, 4), (0, 3), (3, 2), (4, 1), (5, 1)):
         b.set_variant(v)
         b.step(n)
     b.sync()
@@ -189,7 +191,7 @@ def test_batch_equals_individual_steps_d2q9(precision):
         d.step(15)
     b = lbm.Batch(mixed)
     assert b.launches_per_step() == 4            # ghosts, contrast step, plain step, color
-    for v, n in ((2, 3), (1, 3), (0, 5), (3, 2), (4, 2)):
+    for v, n in ((2, 3), (1, 3), (0, 4), (3, 2), (4, 2), (5, 1)):
         b.set_variant(v)
         b.step(n)
     b.sync()
