@@ -812,8 +812,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if sp == 4 else "f32 (f16 population storage)", "data": "synthetic",
             "config": dict(arm_config(n, theta, args.storage, world), nodes=nn, fluid_nodes=fluid, ghost_nodes=ng,
                            l2="inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (lbm.domain_bytes(P, ng) / 1e9)),
-            "roofline": {"bound": "hbm", "kernel": ("k_step<19,float,half,contrast>" if sp == 2
-                                                    else "k_step_pair<19,float,contrast>"),
+            "roofline": {"bound": "hbm", "kernel": "k_step_pair<19,%s,contrast>" % ("half" if sp == 2 else "float"),
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "bytes_per_fluid_node": k_step_bytes_per_fluid_node(Q, D, s, True, sp),

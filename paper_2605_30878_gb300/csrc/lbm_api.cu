@@ -575,15 +575,13 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     c.eps = -(4.0 / P.W) * std::cos(P.theta);
     c.exp_eps = std::exp(c.eps);
     c.ghost_rule = P.ghost_rule;
-    // Float arithmetic: the two-node step kernel with FP32 storage (memory-bound:
-    // half the load/store and address instructions per node raise its
-    // bandwidth, 0.89 -> 0.96 of the measured copy peak at 192^3), the one-node
-    // kernel with FP16 storage (issue-bound: the two-node kernel's halved
-    // occupancy made it 4% slower there).  LBM_STEP_KERNEL=pair|single
-    // overrides; both give the same results to the bit.
+    // Float arithmetic: the two-node step kernel (half the load/store and
+    // address instructions per node: 0.89 -> 0.96 of the measured copy peak
+    // at 192^3 with FP32 storage, 0.61 -> 0.62 of its roofline with FP16
+    // storage).  LBM_STEP_KERNEL=pair|single overrides; both kernels give the
+    // same results to the bit.
     const char* step_kernel = std::getenv("LBM_STEP_KERNEL");
-    c.pair = P.precision != LBM_FP64 && (step_kernel ? std::strcmp(step_kernel, "pair") == 0
-                                                     : P.precision == LBM_FP32);
+    c.pair = P.precision != LBM_FP64 && (step_kernel == nullptr || std::strcmp(step_kernel, "pair") == 0);
 
     // node classes: a solid node with a fluid stencil neighbour is a ghost
     const int64_t nn = L.nn_dense;
