@@ -576,10 +576,10 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     c.exp_eps = std::exp(c.eps);
     c.ghost_rule = P.ghost_rule;
     // Float arithmetic: the two-node step kernel (half the load/store and
-    // address instructions per node: 0.89 -> 0.96 of the measured copy peak
-    // at 192^3 with FP32 storage, 0.61 -> 0.62 of its roofline with FP16
-    // storage).  LBM_STEP_KERNEL=pair|single overrides; both kernels give the
-    // same results to the bit.
+    // address instructions per node of the one-node kernel; at 192^3 0.967
+    // against 0.919 of the measured copy peak with FP32 storage, 0.667 against
+    // 0.658 of its roofline with FP16 storage).  LBM_STEP_KERNEL=pair|single
+    // overrides; both kernels give the same results to the bit.
     const char* step_kernel = std::getenv("LBM_STEP_KERNEL");
     c.pair = P.precision != LBM_FP64 && (step_kernel == nullptr || std::strcmp(step_kernel, "pair") == 0);
 

@@ -456,10 +456,20 @@ __global__ void __launch_bounds__(256) k_ghost(int64_t n_ghosts, const int32_t* 
 // ---------------------------------------------------------------------------
 // k_step: stencils, forces, macroscopic fields, collision, segregation
 // ---------------------------------------------------------------------------
-// Reciprocals: FP64 divides exactly, as the oracle; FP32 uses the correctly
-// rounded hardware-assisted reciprocal and reciprocal square root.
+// Reciprocals: FP64 divides exactly, as the oracle.  FP32 takes the hardware
+// approximation (PTX rcp.approx, within 1 ulp): its operands here (the mixture
+// density, the mixture inverse viscosity, tau) are positive normal floats, so
+// the correctly rounded form's special-case handling buys nothing but
+// instructions, and 1 ulp of these factors is far below the float step's
+// other rounding.
 __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
-__device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rcp(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
 __device__ __forceinline__ double inv_norm_floor(double g2, double floor) {
     const double gn = sqrt(g2);
     return 1.0 / (gn > floor ? gn : floor);
@@ -610,12 +620,34 @@ __device__ __forceinline__ void pull_bounce_back(const StepParams<T>& P, const S
                                                                     (long long)(Q - 1) * pl, err));
 }
 
+// a + k t for an integer coefficient k that is a constant once the direction
+// loops are unrolled: k = 0 emits nothing, k = +/-1 no multiply, and the first
+// term is taken as it is rather than added to a zero (IEEE addition of +0 is
+// not the identity for -0, so the compiler keeps such adds).  The value is the
+// sum the same terms give in the same order, started from zero.
+struct Acc {
+    float v = 0.f;
+    bool set = false;
+    __device__ __forceinline__ void add(int k, float t) {
+        if (k == 0) return;
+        const float kt = k == 1 ? t : (k == -1 ? -t : float(k) * t);
+        v = set ? v + kt : kt;
+        set = true;
+    }
+    __device__ __forceinline__ float get() const { return set ? v : 0.f; }
+};
+
 // ---------------------------------------------------------------------------
 // Float arithmetic of one fluid node, shared by the one-node step kernel and
 // the two-node (pair) kernel, so that both round alike.  Inputs: the pulled
 // populations N (deviations, in storage units with FP16 storage), the color
-// phi at the node and the stencil sums gs[a] = sum_i w_i c_ia (phi_+ - phi_-)
-// over +/- pairs, ls = sum_i w_i (phi(x+c_i) - phi), us[a][b] likewise for u_b.
+// phi at the node and its isotropic stencils gp = grad phi, lap = lap phi and
+// gu[a][b] = d_a u_b (the stencil weights carry the 3 and the 6).
+//
+// Every sum of two products is written as an explicit fmaf (and every other
+// product feeding an add has one use), so that the compiler has no choice of
+// which product to fuse: kernels that inline this code round alike, whatever
+// else they compute around it.
 // ---------------------------------------------------------------------------
 template <int Q, bool UNITS, bool CONTRAST>
 struct FloatNode {
@@ -624,132 +656,149 @@ struct FloatNode {
     static constexpr double w0 = L::w(0);
     // storage units: times sN (N) and sB (B), 2^16 and 2^7 with FP16 storage,
     // else 1.  Being powers of two, the scales fold into the per-node factors
-    // (omega1, the weights, phi, kseg) and the scaled values round exactly as
-    // the unscaled ones would.
+    // (the stress projections, the weights, phi, kseg) and the scaled values
+    // round exactly as the unscaled ones would.
     static constexpr float sN = UNITS ? kScaleN : 1.0f, sB = UNITS ? kScaleB : 1.0f;
     float phi, u[3], uu, p;
     float F[3], gp[3];
     float A0, A1, Axy, Axz, Ayz;               // stress projections of N - Neq, times (1 - 1/tau)
     float base0, base1, base2, three_p, halfF;
     float common1, common2, krc1, krc2;        // per direction class (1 axis, 2 diagonal/edge)
-    float phiB, phmB;
+    float shb1, shb2;                          // (phi - 1/2) chi_i per class, in B's units
+    float phiB;
 
     __device__ __forceinline__ void compute(const StepParams<float>& P, const float (&N)[Q], float phi_,
-                                            float (&gs)[3], float ls, float (&us)[3][3]) {
+                                            const float (&gp_)[3], float lap, const float (&gu)[3][3]) {
         phi = phi_;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            gp[a] = gs[a] * 3.0f;
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb) us[a][bb] *= 3.0f;
-        }
-        const float lap = 6.0f * ls;
+        for (int a = 0; a < 3; ++a) gp[a] = gp_[a];
 
         // mixture density and viscosity (Sec. II), relaxation time (Appendix A)
-        const float rho = P.rho_g + P.drho * phi;
+        const float rho = fmaf(P.drho, phi, P.rho_g);
         const float inv_rho = rcp(rho);
-        const float nu = rcp(phi * P.inv_nu_l + (1.0f - phi) * P.inv_nu_g);
-        const float tau = 0.5f + 3.0f * nu;
+        const float nu = rcp(fmaf(phi, P.inv_nu_l - P.inv_nu_g, P.inv_nu_g));     // 1 / (phi/nu_l + (1-phi)/nu_g)
+        const float tau = fmaf(3.0f, nu, 0.5f);
 
         // force-free velocity, moments and the pressure of this step (Eq. pressureUpdate)
-        float u0[3] = {0.f, 0.f, 0.f};
-        float sum_moving = 0.f;
-        float Pxx = 0.f, Pyy = 0.f, Pzz = 0.f, Pxy = 0.f, Pxz = 0.f, Pyz = 0.f;
+        Acc u0s[3], sm, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
             // odd moments from N_i - N_opp, even ones from N_i + N_opp
             if (L::opp(i) < i) continue;
             const float sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
-            sum_moving += sp;
-            if (cx) { u0[0] += float(cx) * dp; Pxx += sp; }
-            if (cy) { u0[1] += float(cy) * dp; Pyy += sp; }
-            if (cz) { u0[2] += float(cz) * dp; Pzz += sp; }
-            if (cx * cy) Pxy += float(cx * cy) * sp;
-            if (cx * cz) Pxz += float(cx * cz) * sp;
-            if (cy * cz) Pyz += float(cy * cz) * sp;
+            sm.add(1, sp);
+            u0s[0].add(cx, dp);
+            u0s[1].add(cy, dp);
+            u0s[2].add(cz, dp);
+            Pxx.add(cx * cx, sp);
+            Pyy.add(cy * cy, sp);
+            Pzz.add(cz * cz, sp);
+            Pxy.add(cx * cy, sp);
+            Pxz.add(cx * cz, sp);
+            Pyz.add(cy * cz, sp);
         }
-        // FP16 storage: N came in storage units (times 2^16); the moments are linear
-        // in N, so they are scaled back once (exactly, a power of two)
-        if constexpr (UNITS) {
-            constexpr float r = 1.0f / kScaleN;
-            sum_moving *= r;
-            Pxx *= r; Pyy *= r; Pzz *= r; Pxy *= r; Pxz *= r; Pyz *= r;
+        // FP16 storage: N came in storage units (times sN = 2^16); the moments are
+        // linear in N, so the scale is taken out where each is used (exactly, a
+        // power of two): here for u0 and the pressure, in the stress projections
+        // below for the second moments
+        constexpr float r = 1.0f / sN;
+        float u0[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) u0[a] *= r;
-        }
+        for (int a = 0; a < 3; ++a) u0[a] = (a < D) ? (UNITS ? u0s[a].get() * r : u0s[a].get()) : 0.f;
         // Eq. (pressureUpdate) takes sum_{i>0} N_i - (1 - chi_0) with the exact
         // chi; the deviations are stored from the rounded chi of the storage, whose
         // moving values sum to 1 - chi[0], so the difference of the two is
         // chi_0 - chi[0], the rest class's correction (without it the float
         // pressure would sit a constant ~4e-8 off, which F_p = -p grad(rho)
         // turns into a velocity error at a density contrast)
-        const float pres_base = (sum_moving + P.chi_err[0]) * float(1.0 / 3.0);
+        const float pres_base = (UNITS ? fmaf(sm.get(), r, P.chi_err[0]) : sm.get() + P.chi_err[0]) *
+                                float(1.0 / 3.0);
         const float inv_1mw0 = float(1.0 / (1.0 - w0));
-        const float uu0 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
-        const float p0 = (pres_base - float(0.5 * w0) * uu0) * inv_1mw0;
 
-        // forces
-        const float muc = P.k48W * phi * (1.0f - phi) * (phi - 0.5f) + P.k3W2 * lap;   // chemical potential / sigma
+        // forces: surface tension and body force, then (density contrast) the
+        // pressure and viscous corrections
+        const float muc = fmaf(P.k3W2, lap, P.k48W * phi * (1.0f - phi) * (phi - 0.5f));   // chemical potential / sigma
+        const float smu = -P.sigma * muc;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) F[a] = (-P.sigma * muc) * gp[a] + rho * P.g[a];
+        for (int a = 0; a < D; ++a) F[a] = fmaf(smu, gp[a], rho * P.g[a]);
         if (D == 2) F[2] = 0.f;
         if (CONTRAST) {
-            float gr[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) gr[a] = P.drho * gp[a];
-            const float kv = (tau - 0.5f) * float(1.0 / 3.0);
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                float sv = 0.f;
-#pragma unroll
-                for (int bb = 0; bb < D; ++bb) sv += (us[a][bb] + us[bb][a]) * gr[bb];
-                F[a] += kv * sv - p0 * gr[a];
+            // F_p = -p0 grad(rho), F_v = nu (grad u + grad u^T) . grad(rho), grad(rho) = drho grad(phi)
+            const float uu0 = D == 2 ? fmaf(u0[0], u0[0], u0[1] * u0[1])
+                                     : fmaf(u0[0], u0[0], fmaf(u0[1], u0[1], u0[2] * u0[2]));
+            const float p0 = fmaf(-float(0.5 * w0), uu0, pres_base) * inv_1mw0;
+            const float kd = (tau - 0.5f) * float(1.0 / 3.0) * P.drho, pd = -p0 * P.drho;
+            float sv[3];
+            if (D == 2) {
+                const float t01 = gu[0][1] + gu[1][0];
+                sv[0] = fmaf(t01, gp[1], (gu[0][0] + gu[0][0]) * gp[0]);
+                sv[1] = fmaf(t01, gp[0], (gu[1][1] + gu[1][1]) * gp[1]);
+            } else {
+                const float t01 = gu[0][1] + gu[1][0], t02 = gu[0][2] + gu[2][0], t12 = gu[1][2] + gu[2][1];
+                sv[0] = fmaf(t02, gp[2], fmaf(t01, gp[1], (gu[0][0] + gu[0][0]) * gp[0]));
+                sv[1] = fmaf(t12, gp[2], fmaf(t01, gp[0], (gu[1][1] + gu[1][1]) * gp[1]));
+                sv[2] = fmaf(t12, gp[1], fmaf(t02, gp[0], (gu[2][2] + gu[2][2]) * gp[2]));
             }
+#pragma unroll
+            for (int a = 0; a < D; ++a) F[a] = fmaf(kd, sv[a], fmaf(pd, gp[a], F[a]));
         }
 
         // Eq. (velUpdate), Eq. (pressureUpdate)
+        const float hr = 0.5f * inv_rho;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u[a] = u0[a] + 0.5f * F[a] * inv_rho;
-        uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        p = (pres_base - float(0.5 * w0) * uu) * inv_1mw0;
+        for (int a = 0; a < 3; ++a) u[a] = (a < D) ? fmaf(F[a], hr, u0[a]) : 0.f;
+        uu = D == 2 ? fmaf(u[0], u[0], u[1] * u[1]) : fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
+        p = fmaf(-float(0.5 * w0), uu, pres_base) * inv_1mw0;
 
-        // collision: traceless second moments of N - Neq, with sum Neq c c = (c2chi + p) I + u u
-        const float omega1 = UNITS ? (1.0f - rcp(tau)) * sN : 1.0f - rcp(tau);        // 1 - s_nu
+        // collision: traceless second moments of N - Neq, with sum Neq c c = (c2chi + p) I + u u,
+        // in N's storage units (the moments are raw, the u u terms take the scale)
+        const float omega1 = 1.0f - rcp(tau);                                       // 1 - s_nu
+        const float o4 = omega1 * 0.25f;
+        const float pxx = Pxx.get(), pyy = Pyy.get();
+        // (these products enter the direction sums: __fmul_rn keeps the compiler
+        // from fusing them there in one kernel and not in another)
+        base0 = __fmul_rn(3.0f, u[0]);
+        base1 = __fmul_rn(3.0f, u[1]);
+        base2 = __fmul_rn(3.0f, u[2]);
         if (D == 2) {
-            A0 = omega1 * ((Pxx - Pyy) - (u[0] * u[0] - u[1] * u[1])) * 0.25f;     // m7 . f / |m7|^2
+            A0 = __fmul_rn(o4, fmaf(-sN, fmaf(u[0], u[0], -(u[1] * u[1])), pxx - pyy));     // m7 . f / |m7|^2
             A1 = 0.f;
-            Axy = omega1 * (Pxy - u[0] * u[1]) * 0.25f;                             // m8 . f / |m8|^2
+            Axy = __fmul_rn(o4, fmaf(-sN * u[0], u[1], Pxy.get()));                      // m8 . f / |m8|^2
             Axz = Ayz = 0.f;
         } else {
-            A0 = omega1 * ((2.0f * Pxx - Pyy - Pzz) - (2.0f * u[0] * u[0] - u[1] * u[1] - u[2] * u[2])) *
-                 float(1.0 / 36.0);
-            A1 = omega1 * ((Pyy - Pzz) - (u[1] * u[1] - u[2] * u[2])) * float(1.0 / 12.0);
-            Axy = omega1 * (Pxy - u[0] * u[1]) * 0.25f;
-            Axz = omega1 * (Pxz - u[0] * u[2]) * 0.25f;
-            Ayz = omega1 * (Pyz - u[1] * u[2]) * 0.25f;
+            const float pzz = Pzz.get();
+            // 2 ux^2 - uy^2 - uz^2 = 3 ux^2 - u.u
+            A0 = __fmul_rn(omega1 * float(1.0 / 36.0),
+                           fmaf(-sN, fmaf(base0, u[0], -uu), fmaf(2.0f, pxx, -pyy) - pzz));
+            A1 = __fmul_rn(omega1 * float(1.0 / 12.0), fmaf(-sN, fmaf(u[1], u[1], -(u[2] * u[2])), pyy - pzz));
+            const float su0 = -sN * u[0];
+            Axy = __fmul_rn(o4, fmaf(su0, u[1], Pxy.get()));
+            Axz = __fmul_rn(o4, fmaf(su0, u[2], Pxz.get()));
+            Ayz = __fmul_rn(o4, fmaf(-sN * u[1], u[2], Pyz.get()));
         }
 
         // segregation: n_phi = grad phi / max(|grad phi|, 1e-6)
-        const float inv_gn = inv_norm_floor(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2], 1e-6f);
+        const float g2 = D == 2 ? fmaf(gp[0], gp[0], gp[1] * gp[1])
+                                : fmaf(gp[0], gp[0], fmaf(gp[1], gp[1], gp[2] * gp[2]));
+        const float inv_gn = inv_norm_floor(g2, 1e-6f);
         const float kseg = P.two_over_W * phi * (1.0f - phi) * inv_gn;
         const float ksegB = UNITS ? kseg * sB : kseg;                       // recoloring in B's units
         phiB = UNITS ? phi * (sB / sN) : phi;                               // phi N*, from N's units to B's
-        phmB = UNITS ? (phi - 0.5f) * sB : phi - 0.5f;
+        const float phmB = UNITS ? (phi - 0.5f) * sB : phi - 0.5f;
+        shb1 = phmB * P.chi[1];
+        shb2 = phmB * P.chi[D == 2 ? 5 : 7];
         three_p = 3.0f * p;
         halfF = 1.5f * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
-        base0 = 3.0f * u[0];
-        base1 = 3.0f * u[1];
-        base2 = 3.0f * u[2];
-        const float common = three_p - 1.5f * uu;
+        const float common = fmaf(-1.5f, uu, three_p);
         // per direction class (1 axis, 2 diagonal/edge): the equilibrium's constant
         // part w_i (3p - 3u^2/2) + (chi_i - stored chi_i), divided by w_i, and the
         // recolouring weight ksegB (chi_i + w_i 3p) with the exact chi_i
         constexpr double kW1 = L::w(1), kW2 = L::w(D == 2 ? 5 : 7);
-        common1 = common + P.chi_err[1] * float(1.0 / kW1);
-        common2 = common + P.chi_err[2] * float(1.0 / kW2);
-        krc1 = ksegB * ((P.chi[1] + P.chi_err[1]) + float(kW1) * three_p);
-        krc2 = ksegB * ((P.chi[D == 2 ? 5 : 7] + P.chi_err[2]) + float(kW2) * three_p);
+        common1 = fmaf(P.chi_err[1], float(1.0 / kW1), common);
+        common2 = fmaf(P.chi_err[2], float(1.0 / kW2), common);
+        krc1 = ksegB * fmaf(float(kW1), three_p, P.chi[1] + P.chi_err[1]);
+        krc2 = ksegB * fmaf(float(kW2), three_p, P.chi[D == 2 ? 5 : 7] + P.chi_err[2]);
     }
 
     // Direction i (opp(i) > i) and its opposite o, in storage units: the
@@ -760,36 +809,42 @@ struct FloatNode {
                                         float& bo) const {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const float wiN = float(L::w(i)) * sN;
-        float proj;
+        // the stress projection, 3 c.u, c.F and c.grad phi, each without the terms
+        // whose lattice coefficient is zero
+        Acc proj, cu3, cF, cg;
         if (D == 2) {
-            proj = float(cx * cx - cy * cy) * A0 + float(cx * cy) * Axy;
+            proj.add(cx * cx - cy * cy, A0);
+            proj.add(cx * cy, Axy);
         } else {
             const int c2 = cx * cx + cy * cy + cz * cz;
-            proj = float(3 * cx * cx - c2) * A0 + float(cy * cy - cz * cz) * A1 + float(cx * cy) * Axy +
-                   float(cx * cz) * Axz + float(cy * cz) * Ayz;
+            proj.add(3 * cx * cx - c2, A0);
+            proj.add(cy * cy - cz * cz, A1);
+            proj.add(cx * cy, Axy);
+            proj.add(cx * cz, Axz);
+            proj.add(cy * cz, Ayz);
         }
-        float cu3 = 0.f, cF = 0.f, cg = 0.f;   // 3 c.u, c.F, c.grad phi
-        if (cx) { cu3 += float(cx) * base0; cF += float(cx) * F[0]; cg += float(cx) * gp[0]; }
-        if (cy) { cu3 += float(cy) * base1; cF += float(cy) * F[1]; cg += float(cy) * gp[1]; }
-        if (cz) { cu3 += float(cz) * base2; cF += float(cz) * F[2]; cg += float(cz) * gp[2]; }
+        cu3.add(cx, base0); cF.add(cx, F[0]); cg.add(cx, gp[0]);
+        cu3.add(cy, base1); cF.add(cy, F[1]); cg.add(cy, gp[1]);
+        cu3.add(cz, base2); cF.add(cz, F[2]); cg.add(cz, gp[2]);
         const bool axis = cx * cx + cy * cy + cz * cz == 1;
-        const float rc = (axis ? krc1 : krc2) * cg;                    // recoloring, odd in c
-        const float even = wiN * ((axis ? common1 : common2) + 0.5f * cu3 * cu3) + proj;
-        const float odd = wiN * (cu3 + halfF * cF);
-        ni = even + odd;
-        no = even - odd;
-        const float shift_b = phmB * P.chi[i];
-        bi = phiB * ni + shift_b + rc;
-        bo = phiB * no + shift_b - rc;
+        const float krc = axis ? krc1 : krc2, g = cg.get();            // recoloring krc (c . grad phi), odd in c
+        const float c3 = cu3.get();
+        const float even = fmaf(wiN, fmaf(0.5f * c3, c3, axis ? common1 : common2), proj.get());
+        const float odd = fmaf(halfF, cF.get(), c3);                   // the odd part over wiN
+        ni = fmaf(wiN, odd, even);
+        no = fmaf(-wiN, odd, even);
+        const float shift_b = axis ? shb1 : shb2;                      // (phi - 1/2) chi_i
+        bi = fmaf(krc, g, fmaf(phiB, ni, shift_b));
+        bo = fmaf(-krc, g, fmaf(phiB, no, shift_b));
     }
 
     // Rest direction (no forcing, no stress projection, no recoloring, c_0 = 0),
     // stored exactly (FP32): N*_0 - chi_0 and B*_0 - chi_0/2.
     __device__ __forceinline__ float rest_N(const StepParams<float>& P) const {
-        return P.chi_err[0] - float(1.0 - w0) * three_p - float(1.5 * w0) * uu;
+        return fmaf(-float(1.5 * w0), uu, fmaf(-float(1.0 - w0), three_p, P.chi_err[0]));
     }
     __device__ __forceinline__ float rest_B(const StepParams<float>& P, float nst0) const {
-        return phi * nst0 + (phi - 0.5f) * P.chi[0];
+        return fmaf(phi, nst0, (phi - 0.5f) * P.chi[0]);
     }
     // With FP16 storage the float rest populations take the node totals the
     // collision fixes less the moving populations as stored (sumN, sumB in
@@ -799,7 +854,9 @@ struct FloatNode {
     // recoloring is odd in c), so FP16 rounding moves no mass between the
     // phases or out of the domain.
     __device__ __forceinline__ static float rest_N_from_sum(float sumN) { return -sumN * (1.0f / kScaleN); }
-    __device__ __forceinline__ float rest_B_from_sum(float sumB) const { return (phi - 0.5f) - sumB * (1.0f / kScaleB); }
+    __device__ __forceinline__ float rest_B_from_sum(float sumB) const {
+        return fmaf(-sumB, 1.0f / kScaleB, phi - 0.5f);
+    }
 };
 
 // One fluid node of the step: pulled populations N, the block's halo tile.
@@ -838,18 +895,20 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
             // multiply-add by the constant c_ia w_i
             const T pp = s_phi[idx_checked(hp, Tl::HN, err)], pm = s_phi[idx_checked(hm, Tl::HN, err)];
             const T dphi = pp - pm;
-            if (cx) gp[0] += (T(cx) * wi) * dphi;
-            if (cy) gp[1] += (T(cy) * wi) * dphi;
-            if (cz) gp[2] += (T(cz) * wi) * dphi;
-            lsum += wi * ((pp - phi) + (pm - phi));
+            // the weights carry the 3 of the gradient and the 6 of the laplacian
+            const T g3 = T(3.0 * L::w(i)), l6 = T(6.0 * L::w(i));
+            if (cx) gp[0] = fmadd(T(cx) * g3, dphi, gp[0]);
+            if (cy) gp[1] = fmadd(T(cy) * g3, dphi, gp[1]);
+            if (cz) gp[2] = fmadd(T(cz) * g3, dphi, gp[2]);
+            lsum = fmadd(l6, (pp - phi) + (pm - phi), lsum);
             if (CONTRAST) {
 #pragma unroll
                 for (int bb = 0; bb < D; ++bb) {
                     const T dub = s_u[idx_checked(bb * Tl::HN + hp, D * Tl::HN, err)] -
                                   s_u[idx_checked(bb * Tl::HN + hm, D * Tl::HN, err)];
-                    if (cx) du[0][bb] += (T(cx) * wi) * dub;
-                    if (cy) du[1][bb] += (T(cy) * wi) * dub;
-                    if (cz) du[2][bb] += (T(cz) * wi) * dub;
+                    if (cx) du[0][bb] = fmadd(T(cx) * g3, dub, du[0][bb]);
+                    if (cy) du[1][bb] = fmadd(T(cy) * g3, dub, du[1][bb]);
+                    if (cz) du[2][bb] = fmadd(T(cz) * g3, dub, du[2][bb]);
                 }
             }
         } else {

@@ -139,24 +139,24 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const float wi = float(L::w(i));
+        const float wi = float(3.0 * L::w(i)), wl = float(6.0 * L::w(i));   // grad: 3 w_i, lap: 6 w_i
         const int o = Tl::off(cx, cy, cz);
         const float2 pp = halo_pair<Tl::HN>(s_phi, hcA, o, err), pm = halo_pair<Tl::HN>(s_phi, hcA, -o, err);
         const float dphiA = pp.x - pm.x, dphiB = pp.y - pm.y;
-        if (cx) { gA[0] += (float(cx) * wi) * dphiA; gB[0] += (float(cx) * wi) * dphiB; }
-        if (cy) { gA[1] += (float(cy) * wi) * dphiA; gB[1] += (float(cy) * wi) * dphiB; }
-        if (cz) { gA[2] += (float(cz) * wi) * dphiA; gB[2] += (float(cz) * wi) * dphiB; }
-        lA += wi * ((pp.x - ph.x) + (pm.x - ph.x));
-        lB += wi * ((pp.y - ph.y) + (pm.y - ph.y));
+        if (cx) { gA[0] = fmaf(float(cx) * wi, dphiA, gA[0]); gB[0] = fmaf(float(cx) * wi, dphiB, gB[0]); }
+        if (cy) { gA[1] = fmaf(float(cy) * wi, dphiA, gA[1]); gB[1] = fmaf(float(cy) * wi, dphiB, gB[1]); }
+        if (cz) { gA[2] = fmaf(float(cz) * wi, dphiA, gA[2]); gB[2] = fmaf(float(cz) * wi, dphiB, gB[2]); }
+        lA = fmaf(wl, (pp.x - ph.x) + (pm.x - ph.x), lA);
+        lB = fmaf(wl, (pp.y - ph.y) + (pm.y - ph.y), lB);
         if (CONTRAST) {
 #pragma unroll
             for (int bb = 0; bb < D; ++bb) {
                 const float2 up = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, o, err);
                 const float2 um = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, -o, err);
                 const float duA = up.x - um.x, duB = up.y - um.y;
-                if (cx) { dA[0][bb] += (float(cx) * wi) * duA; dB[0][bb] += (float(cx) * wi) * duB; }
-                if (cy) { dA[1][bb] += (float(cy) * wi) * duA; dB[1][bb] += (float(cy) * wi) * duB; }
-                if (cz) { dA[2][bb] += (float(cz) * wi) * duA; dB[2][bb] += (float(cz) * wi) * duB; }
+                if (cx) { dA[0][bb] = fmaf(float(cx) * wi, duA, dA[0][bb]); dB[0][bb] = fmaf(float(cx) * wi, duB, dB[0][bb]); }
+                if (cy) { dA[1][bb] = fmaf(float(cy) * wi, duA, dA[1][bb]); dB[1][bb] = fmaf(float(cy) * wi, duB, dB[1][bb]); }
+                if (cz) { dA[2][bb] = fmaf(float(cz) * wi, duA, dA[2][bb]); dB[2][bb] = fmaf(float(cz) * wi, duB, dB[2][bb]); }
             }
         }
     }
