@@ -204,7 +204,9 @@ lbm_status lbm_diagnostics(lbm_domain* dom, const lbm_probe* probe, lbm_diag* ou
 
 /* Copy one state field to / from a host double array laid out as in
  * lbm_field (FP32 domains convert).  read synchronises; write is ordered
- * before later work on the domain stream and returns after the copy. */
+ * before later work on the domain stream and returns after the copy.
+ * Populations read back as 0 at non-fluid nodes; a written velocity is taken
+ * as 0 there (the stencils read it as the wall's velocity). */
 lbm_status lbm_read_state(lbm_domain* dom, int32_t field, double* host_out);
 lbm_status lbm_write_state(lbm_domain* dom, int32_t field, const double* host_in);
 

@@ -1,13 +1,18 @@
 // Host side of the C ABI declared in include/lbm.h: validation, ghost-table
 // preparation (x_F = x_G + n_s, Fig. 2), device memory layout, CUDA-graph
 // step replay, state transfer and diagnostics.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda.h>
@@ -102,8 +107,18 @@ struct lbm_domain {
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;
     int64_t ng = 0, n_fallback = 0, n_fluid = 0;
-    std::vector<uint8_t> h_cls;
-    std::vector<int32_t> h_corner;   // [GK][ng]
+    // node classes on the host as row bit masks: row r = y + ny z, W words of
+    // 64 nodes each, bit x of fluid[r W + x / 64] (ghost[...]) set for a fluid
+    // (ghost) node
+    int row_words = 0;
+    std::vector<uint64_t> fluid_bits, ghost_bits;
+    bool is_fluid(int64_t node) const {          // dense node index
+        const int64_t nx = prm.nx, r = node / nx, x = node - r * nx;
+        return (fluid_bits[(size_t)(r * row_words + (x >> 6))] >> (x & 63)) & 1u;
+    }
+    std::vector<int32_t> h_corner;   // [GK][ng], dense node indices
+    std::vector<int32_t> h_pcorner;  // [GK][ng], padded (device) node indices
+    std::vector<int32_t> h_pnode;    // [ng], padded ghost nodes
     std::vector<double> h_wt;        // [GK][ng]
     std::vector<int32_t> h_nc;
     StepConfig cfg;
@@ -135,9 +150,199 @@ struct lbm_domain {
 
 namespace {
 // device index of grid node x + nx * (y + ny * z): x + px * (y + ny * z)
-int64_t padded_node(const lbm_domain* d, int64_t node) {
-    const int64_t nx = d->prm.nx;
-    return node % nx + (int64_t)d->lay.px * (node / nx);
+
+// Host threads for the per-domain set-up work (node classes, ghost
+// weights).  Starting a thread costs tens of microseconds, as much as the
+// work itself on a 192^3 grid, so the threads are started once, on first
+// use, and sleep between calls.  The pool is never destroyed: its threads
+// live as long as the process.  run() calls are serialised; the caller's
+// thread works too, so a pool whose threads could not be started (or a
+// forked child, which has none) still finishes every call.
+class HostPool {
+public:
+    static HostPool& get() {
+        static HostPool* pool = new HostPool();
+        return *pool;
+    }
+    int threads() const { return workers_ + 1; }
+    // fn(i) for every i in [0, n), on the pool's threads and the caller's
+    void run(int n, const std::function<void(int)>& fn) {
+        std::lock_guard<std::mutex> one_call(call_);
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            fn_ = &fn;
+            n_ = n;
+            next_ = 0;
+            done_ = 0;
+            ++gen_;
+        }
+        wake_.notify_all();
+        work();
+        std::unique_lock<std::mutex> lk(m_);
+        finished_.wait(lk, [&] { return done_ == n_; });
+        fn_ = nullptr;
+    }
+
+private:
+    HostPool() {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int want = std::min<int>(hw > 1 ? (int)hw - 1 : 0, 15);
+        for (int t = 0; t < want; ++t) {
+            try {
+                std::thread(&HostPool::loop, this).detach();
+                ++workers_;
+            } catch (...) {
+                break;
+            }
+        }
+    }
+    void work() {
+        for (;;) {
+            const std::function<void(int)>* fn;
+            int i;
+            {
+                std::lock_guard<std::mutex> lk(m_);
+                if (!fn_ || next_ >= n_) return;
+                fn = fn_;
+                i = next_++;
+            }
+            (*fn)(i);
+            std::lock_guard<std::mutex> lk(m_);
+            if (++done_ == n_) finished_.notify_all();
+        }
+    }
+    void loop() {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(m_);
+                wake_.wait(lk, [&] { return gen_ != seen; });
+                seen = gen_;
+            }
+            work();
+        }
+    }
+    std::mutex call_, m_;
+    std::condition_variable wake_, finished_;
+    const std::function<void(int)>* fn_ = nullptr;
+    int n_ = 0, next_ = 0, done_ = 0, workers_ = 0;
+    uint64_t gen_ = 0;
+};
+
+// The number of chunks for n items of at least min_chunk each, at most one
+// per pool thread (and at most 16: the callers keep per-chunk counters).
+int64_t chunk_count(int64_t n, int64_t min_chunk) {
+    const int64_t k = std::min<int64_t>(HostPool::get().threads(), 16);
+    return std::max<int64_t>(1, std::min<int64_t>(k, n / std::max<int64_t>(min_chunk, 1)));
+}
+
+// f(begin, end, chunk) over [0, n) in contiguous chunks of at least min_chunk
+// items on the pool's threads; returns the number of chunks.
+template <class F>
+int parallel_chunks(int64_t n, int64_t min_chunk, F f) {
+    const int64_t k = chunk_count(n, min_chunk);
+    if (k == 1) {
+        f((int64_t)0, n, 0);
+        return 1;
+    }
+    HostPool::get().run((int)k, [&](int c) { f(n * c / k, n * (c + 1) / k, c); });
+    return (int)k;
+}
+
+// f1 over the chunks of [0, n), then, once every f1 has returned, f2 over the
+// same chunks.
+template <class F1, class F2>
+void parallel_phases(int64_t n, int64_t min_chunk, F1 f1, F2 f2) {
+    const int64_t k = chunk_count(n, min_chunk);
+    if (k == 1) {
+        f1((int64_t)0, n, 0);
+        f2((int64_t)0, n, 0);
+        return;
+    }
+    HostPool::get().run((int)k, [&](int c) { f1(n * c / k, n * (c + 1) / k, c); });
+    HostPool::get().run((int)k, [&](int c) { f2(n * c / k, n * (c + 1) / k, c); });
+}
+
+// Bit k of the result: byte k of v (little-endian order, as on every target
+// here) is nonzero.  The shifts OR each byte's bits into its bit 0; the
+// multiply moves bit 8k to bit 56 + k (the partial products fall on distinct
+// bits, so nothing carries).
+inline uint64_t nonzero_byte_bits(uint64_t v) {
+    v |= v >> 4;
+    v |= v >> 2;
+    v |= v >> 1;
+    return ((v & 0x0101010101010101ull) * 0x0102040810204080ull) >> 56;
+}
+
+// Node classes of a grid as row bit masks (see lbm_domain): a solid node with
+// a fluid stencil neighbour (periodic wrap on every axis; a non-periodic axis
+// has solid end layers, so its wrap finds no fluid) is a ghost.  The stencil
+// of a row is the row itself shifted by +/-1 in x, the four rows next to it
+// in y and z, shifted by -1, 0, +1 (axis and x-edge directions), and in 3D
+// the four rows diagonal in (y, z) (the yz-edge directions).  Rows are split
+// over host threads; n_solid and n_ghost count the grid's solid and ghost
+// nodes.
+void classify_rows(const lbm_params& P, const uint8_t* solid, int W, std::vector<uint64_t>& F,
+                   std::vector<uint64_t>& G, int64_t& n_solid, int64_t& n_ghost) {
+    const int64_t nx = P.nx, ny = P.ny, nz = P.nz, rows = ny * nz;
+    const uint64_t last = (nx & 63) ? (1ull << (nx & 63)) - 1 : ~0ull;   // valid bits of a row's last word
+    F.assign((size_t)(rows * W), 0);
+    G.assign((size_t)(rows * W), 0);
+    const bool three_d = P.lattice == LBM_D3Q19;
+    std::vector<int64_t> solid_n(16, 0), ghost_n(16, 0);
+    // at least ~1M nodes per chunk (measured: smaller chunks ran slower)
+    const int64_t min_rows = std::max<int64_t>(1, ((int64_t)1 << 20) / nx);
+    parallel_phases(rows, min_rows, [&](int64_t r0, int64_t r1, int) {
+        for (int64_t r = r0; r < r1; ++r) {
+            const uint8_t* row = solid + nx * r;
+            uint64_t* f = &F[(size_t)(r * W)];
+            int64_t x = 0;
+            for (; x + 8 <= nx; x += 8) {
+                uint64_t v;
+                std::memcpy(&v, row + x, 8);
+                f[x >> 6] |= nonzero_byte_bits(v) << (x & 63);
+            }
+            for (; x < nx; ++x) f[x >> 6] |= (uint64_t)(row[x] != 0) << (x & 63);
+            for (int w = 0; w < W; ++w) f[w] = ~f[w];                       // solid -> fluid bits
+            f[W - 1] &= last;
+        }
+    }, [&](int64_t r0, int64_t r1, int chunk) {
+        std::vector<uint64_t> A(W), B(W);
+        int64_t ns = 0, ng = 0;
+        for (int64_t r = r0; r < r1; ++r) {
+            const int64_t y = r % ny, z = r / ny;
+            const int64_t ym = (y + ny - 1) % ny, yp = (y + 1) % ny, zm = (z + nz - 1) % nz, zp = (z + 1) % nz;
+            const uint64_t* fr = &F[(size_t)(r * W)];
+            auto row_of = [&](int64_t yy, int64_t zz) { return &F[(size_t)((yy + ny * zz) * W)]; };
+            const uint64_t *fa = row_of(ym, z), *fb = row_of(yp, z);
+            const uint64_t *fc = three_d ? row_of(y, zm) : fr, *fd = three_d ? row_of(y, zp) : fr;
+            for (int w = 0; w < W; ++w) {
+                A[w] = fa[w] | fb[w] | (three_d ? fc[w] | fd[w] : 0);
+                B[w] = fr[w] | A[w];
+            }
+            // shifted copies of B: bit x <- bit x - 1 and bit x <- bit x + 1, periodic in x
+            uint64_t carry = (B[(nx - 1) >> 6] >> ((nx - 1) & 63)) & 1u;
+            uint64_t* g = &G[(size_t)(r * W)];
+            for (int w = 0; w < W; ++w) {
+                const uint64_t up = (B[w] << 1) | carry;
+                carry = B[w] >> 63;
+                const uint64_t down = (B[w] >> 1) | (w + 1 < W ? B[w + 1] << 63 : 0);
+                uint64_t n = up | down | A[w];
+                if (three_d) n |= row_of(ym, zm)[w] | row_of(yp, zm)[w] | row_of(ym, zp)[w] | row_of(yp, zp)[w];
+                g[w] = ~fr[w] & n;
+            }
+            g[(nx - 1) >> 6] |= ~fr[(nx - 1) >> 6] & ((B[0] & 1u) << ((nx - 1) & 63));   // x = nx-1 sees x = 0
+            g[W - 1] &= last;
+            for (int w = 0; w < W; ++w) {
+                ns += __builtin_popcountll(~fr[w] & (w == W - 1 ? last : ~0ull));
+                ng += __builtin_popcountll(g[w]);
+            }
+        }
+        solid_n[chunk] = ns;
+        ghost_n[chunk] = ng;
+    });
+    n_solid = n_ghost = 0;
+    for (int k = 0; k < 16; ++k) { n_solid += solid_n[k]; n_ghost += ghost_n[k]; }
 }
 }  // namespace
 
@@ -208,87 +413,137 @@ void color_weights(int Q, double M_phi, double chi[19], double& alpha, double& c
     c2chi = (1.0 - alpha) * cs2 / (1.0 - w0);
 }
 
+// f(k) for every fluid node k (dense index) of the domain, from the row bits
+template <class F>
+void for_fluid_nodes(const lbm_domain* d, F f) {
+    const int64_t nx = d->prm.nx, rows = (int64_t)d->prm.ny * d->prm.nz;
+    const int W = d->row_words;
+    for (int64_t r = 0; r < rows; ++r)
+        for (int w = 0; w < W; ++w) {
+            uint64_t bits = d->fluid_bits[(size_t)(r * W + w)];
+            while (bits) {
+                const int b = __builtin_ctzll(bits);
+                bits &= bits - 1;
+                f(r * nx + 64 * w + b);
+            }
+        }
+}
+
 lbm_status prepare_ghosts(lbm_domain* d, const lbm_ghost* ghosts) {
     const lbm_params& P = d->prm;
-    const int D = d->lay.D, GK = d->lay.GK;
-    const int64_t ng = d->ng, nx = P.nx, ny = P.ny, nz = P.nz;
+    const int D = d->lay.D, GK = d->lay.GK, W = d->row_words;
+    const int64_t ng = d->ng, nx = P.nx, ny = P.ny, px = d->lay.px;
     const int dims[3] = {P.nx, P.ny, P.nz};
     d->h_corner.assign((size_t)GK * ng, 0);
+    d->h_pcorner.assign((size_t)GK * ng, 0);
+    d->h_pnode.assign((size_t)ng, 0);
     d->h_wt.assign((size_t)GK * ng, 0.0);
     d->h_nc.assign(ng, 0);
     std::vector<int> ox, oy, oz;
     stencil_offsets(P.lattice, ox, oy, oz);
-    std::vector<uint8_t> seen(d->lay.nn_dense, 0);
+    auto fluid_at = [&](int64_t x, int64_t y, int64_t z) {
+        return (d->fluid_bits[(size_t)((y + ny * z) * W + (x >> 6))] >> (x & 63)) & 1u;
+    };
+    // validation, in list order (the first bad entry is the one reported); a
+    // listed ghost's bit is cleared in a copy of the ghost bits, which catches
+    // a second listing of the same node
+    std::vector<uint64_t> unlisted(d->ghost_bits);
     for (int64_t g = 0; g < ng; ++g) {
         const int64_t node = ghosts[g].node;
-        if (node < 0 || node >= d->lay.nn_dense || d->h_cls[node] != CLS_GHOST)
+        bool ghost = false, listed = false;
+        if (node >= 0 && node < d->lay.nn_dense) {
+            const int64_t r = node / nx, x = node - r * nx;
+            const size_t w = (size_t)(r * W + (x >> 6));
+            ghost = (d->ghost_bits[w] >> (x & 63)) & 1u;
+            listed = ghost && !((unlisted[w] >> (x & 63)) & 1u);
+            unlisted[w] &= ~(1ull << (x & 63));
+        }
+        if (listed) return fail(nullptr, LBM_ERR_ARG, "node " + std::to_string(node) + " is listed twice");
+        if (!ghost)
             return fail(nullptr, LBM_ERR_ARG, "ghost " + std::to_string(g) + " (node " + std::to_string(node) +
                                                   ") is not a solid node with a fluid neighbour");
-        if (seen[node]) return fail(nullptr, LBM_ERR_ARG, "node " + std::to_string(node) + " is listed twice");
-        seen[node] = 1;
         const double* n = ghosts[g].n;
         const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         if (!(std::fabs(len - 1.0) <= 1e-6))
             return fail(nullptr, LBM_ERR_ARG, "ghost " + std::to_string(g) + " normal is not a unit vector");
         if (D == 2 && n[2] != 0.0)
             return fail(nullptr, LBM_ERR_ARG, "ghost " + std::to_string(g) + " has a z normal on a 2D lattice");
-        const int64_t xyz[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
-        // x_F = x_G + n_s; its cell corners and bilinear/trilinear weights
-        double base[3] = {0, 0, 0}, frac[3] = {0, 0, 0};
-        for (int a = 0; a < D; ++a) {
-            const double xf = (double)xyz[a] + n[a];
-            base[a] = std::floor(xf);
-            frac[a] = xf - base[a];
-        }
-        int kept = 0;
-        double wsum = 0.0;
-        int32_t cidx[8];
-        double cw[8];
-        for (int k = 0; k < (1 << D); ++k) {
-            int64_t c[3] = {0, 0, 0};
-            double wk = 1.0;
-            for (int a = 0; a < D; ++a) {
-                const int bit = (k >> a) & 1;
-                int64_t v = (int64_t)base[a] + bit;       // within one cell of the ghost: x - 1 .. x + 2
-                while (v < 0) v += dims[a];
-                while (v >= dims[a]) v -= dims[a];
-                c[a] = v;
-                wk *= bit ? frac[a] : 1.0 - frac[a];
-            }
-            const int64_t cn = c[0] + nx * (c[1] + ny * c[2]);
-            if (d->h_cls[cn] == CLS_FLUID) {
-                cidx[kept] = (int32_t)cn;
-                cw[kept] = wk;
-                wsum += wk;
-                ++kept;
-            }
-        }
-        if (kept > 0 && wsum > 0.0) {
-            for (int k = 0; k < kept; ++k) cw[k] /= wsum;
-        } else {
-            // the fluid stencil neighbour most aligned with n_s; ties -> smaller node index
-            int64_t best = -1;
-            double best_dot = -INFINITY;
-            for (size_t j = 0; j < ox.size(); ++j) {
-                int64_t c[3] = {xyz[0] + ox[j], xyz[1] + oy[j], xyz[2] + oz[j]};
-                for (int a = 0; a < 3; ++a) { c[a] %= dims[a]; if (c[a] < 0) c[a] += dims[a]; }
-                const int64_t cn = c[0] + nx * (c[1] + ny * c[2]);
-                if (d->h_cls[cn] != CLS_FLUID) continue;
-                const double dot = ox[j] * n[0] + oy[j] * n[1] + oz[j] * n[2];
-                if (dot > best_dot || (dot == best_dot && cn < best)) { best_dot = dot; best = cn; }
-            }
-            kept = 1;
-            cidx[0] = (int32_t)best;
-            cw[0] = 1.0;
-            d->n_fallback++;
-        }
-        d->h_nc[g] = kept;
-        for (int k = 0; k < GK; ++k) {
-            d->h_corner[(size_t)k * ng + g] = k < kept ? cidx[k] : cidx[0];
-            d->h_wt[(size_t)k * ng + g] = k < kept ? cw[k] : 0.0;
-        }
     }
-    (void)nz;
+
+    // x_F = x_G + n_s, its cell corners and their bilinear/trilinear weights;
+    // independent per ghost, so the list is split over host threads.  Node
+    // indices are kept dense (lbm_ghost_table) and padded (the device).
+    std::vector<int64_t> fallbacks(16, 0);
+    parallel_chunks(ng, 2048, [&](int64_t g0, int64_t g1, int chunk) {
+        int64_t n_fb = 0;
+        for (int64_t g = g0; g < g1; ++g) {
+            const int64_t node = ghosts[g].node;
+            const double* n = ghosts[g].n;
+            const int64_t xyz[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
+            d->h_pnode[g] = (int32_t)(xyz[0] + px * (xyz[1] + ny * xyz[2]));
+            double base[3] = {0, 0, 0}, frac[3] = {0, 0, 0};
+            for (int a = 0; a < D; ++a) {
+                const double xf = (double)xyz[a] + n[a];
+                base[a] = std::floor(xf);
+                frac[a] = xf - base[a];
+            }
+            int kept = 0;
+            double wsum = 0.0;
+            int64_t cidx[8], cpad[8];
+            double cw[8];
+            for (int k = 0; k < (1 << D); ++k) {
+                int64_t c[3] = {0, 0, 0};
+                double wk = 1.0;
+                for (int a = 0; a < D; ++a) {
+                    const int bit = (k >> a) & 1;
+                    int64_t v = (int64_t)base[a] + bit;       // within one cell of the ghost: x - 1 .. x + 2
+                    while (v < 0) v += dims[a];
+                    while (v >= dims[a]) v -= dims[a];
+                    c[a] = v;
+                    wk *= bit ? frac[a] : 1.0 - frac[a];
+                }
+                if (fluid_at(c[0], c[1], c[2])) {
+                    cidx[kept] = c[0] + nx * (c[1] + ny * c[2]);
+                    cpad[kept] = c[0] + px * (c[1] + ny * c[2]);
+                    cw[kept] = wk;
+                    wsum += wk;
+                    ++kept;
+                }
+            }
+            if (kept > 0 && wsum > 0.0) {
+                for (int k = 0; k < kept; ++k) cw[k] /= wsum;
+            } else {
+                // the fluid stencil neighbour most aligned with n_s; ties -> smaller node index
+                int64_t best = -1, best_pad = -1;
+                double best_dot = -INFINITY;
+                for (size_t j = 0; j < ox.size(); ++j) {
+                    int64_t c[3] = {xyz[0] + ox[j], xyz[1] + oy[j], xyz[2] + oz[j]};
+                    for (int a = 0; a < 3; ++a) { c[a] %= dims[a]; if (c[a] < 0) c[a] += dims[a]; }
+                    if (!fluid_at(c[0], c[1], c[2])) continue;
+                    const int64_t cn = c[0] + nx * (c[1] + ny * c[2]);
+                    const double dot = ox[j] * n[0] + oy[j] * n[1] + oz[j] * n[2];
+                    if (dot > best_dot || (dot == best_dot && cn < best)) {
+                        best_dot = dot;
+                        best = cn;
+                        best_pad = c[0] + px * (c[1] + ny * c[2]);
+                    }
+                }
+                kept = 1;
+                cidx[0] = best;
+                cpad[0] = best_pad;
+                cw[0] = 1.0;
+                ++n_fb;
+            }
+            d->h_nc[g] = kept;
+            for (int k = 0; k < GK; ++k) {
+                d->h_corner[(size_t)k * ng + g] = (int32_t)(k < kept ? cidx[k] : cidx[0]);
+                d->h_pcorner[(size_t)k * ng + g] = (int32_t)(k < kept ? cpad[k] : cpad[0]);
+                d->h_wt[(size_t)k * ng + g] = k < kept ? cw[k] : 0.0;
+            }
+        }
+        fallbacks[chunk] = n_fb;
+    });
+    for (int64_t f : fallbacks) d->n_fallback += f;
     return LBM_OK;
 }
 
@@ -480,12 +735,17 @@ lbm_status init_state(lbm_domain* d, int mode, const double ctr[3], double R0) {
     d->cur = 0;
     d->step = 0;
     const Layout& L = d->lay;
+    // What a step reads is set here: the populations of the fluid nodes
+    // (init_pops) and the velocity of the first step's stencil, 0.  Population
+    // slots of non-fluid nodes are never read (every pull of a fluid node reads
+    // a fluid source or the node's own slots, as the diagnostics and state
+    // transfer do), the second velocity buffer is written at every fluid node
+    // by the first step, and the velocity of non-fluid nodes stays 0 from the
+    // domain's creation (no kernel writes it but as 0).  So of the state only
+    // the first velocity buffer and p (state read back as 0 before a step) are
+    // cleared.
     CUDA_TRY(d, cudaMemsetAsync(d->errflag(), 0, sizeof(int), d->stream));
-    for (int k = 0; k < 2; ++k) {
-        CUDA_TRY(d, cudaMemsetAsync(d->U(k), 0, (size_t)L.D * L.plane * L.elem, d->stream));
-        CUDA_TRY(d, cudaMemsetAsync(d->N(k), 0, L.pop_bytes, d->stream));
-        CUDA_TRY(d, cudaMemsetAsync(d->B(k), 0, L.pop_bytes, d->stream));
-    }
+    CUDA_TRY(d, cudaMemsetAsync(d->U(0), 0, (size_t)L.D * L.plane * L.elem, d->stream));
     CUDA_TRY(d, cudaMemsetAsync(d->p(), 0, (size_t)L.plane * L.elem, d->stream));
     dispatch(d, [&](auto Lx) {
         decltype(Lx)::init_phi(d->cfg, d->cls(), d->phi(), mode, ctr, R0, ghost_value, d->stream);
@@ -583,49 +843,31 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     const char* step_kernel = std::getenv("LBM_STEP_KERNEL");
     c.pair = P.precision != LBM_FP64 && (step_kernel == nullptr || std::strcmp(step_kernel, "pair") == 0);
 
-    // node classes: a solid node with a fluid stencil neighbour is a ghost
+    // node classes, as row bit masks on the host (the device expands them)
     const int64_t nn = L.nn_dense;
     const int64_t nx = P.nx, ny = P.ny, nz = P.nz;
-    d->h_cls.assign(nn, CLS_FLUID);
-    std::vector<int> ox, oy, oz;
-    stencil_offsets(P.lattice, ox, oy, oz);
+    d->row_words = (int)((nx + 63) / 64);
     int64_t n_cls_ghost = 0, n_solid = 0;
-    uint8_t* cls_out = d->h_cls.data();
-    for (int64_t z = 0; z < nz; ++z)
-        for (int64_t y = 0; y < ny; ++y) {
-            const uint8_t* row = solid + nx * (y + ny * z);
-            for (int64_t x = 0; x < nx; ++x) {
-                if (!row[x]) {                          // fluid: the class array starts as all fluid
-                    if ((x & 7) == 0 && x + 8 <= nx) {  // skip eight fluid nodes at a time
-                        uint64_t w;
-                        std::memcpy(&w, row + x, 8);
-                        if (w == 0) x += 7;
-                    }
-                    continue;
-                }
-                ++n_solid;
-                uint8_t cl = CLS_SOLID;
-                for (size_t j = 0; j < ox.size(); ++j) {
-                    int64_t xx = x + ox[j], yy = y + oy[j], zz = z + oz[j];
-                    xx += xx < 0 ? nx : (xx >= nx ? -nx : 0);
-                    yy += yy < 0 ? ny : (yy >= ny ? -ny : 0);
-                    zz += zz < 0 ? nz : (zz >= nz ? -nz : 0);
-                    if (!solid[xx + nx * (yy + ny * zz)]) { cl = CLS_GHOST; break; }
-                }
-                cls_out[x + nx * (y + ny * z)] = cl;
-                n_cls_ghost += cl == CLS_GHOST;
-            }
-        }
+    classify_rows(P, solid, d->row_words, d->fluid_bits, d->ghost_bits, n_solid, n_cls_ghost);
     d->n_fluid = nn - n_solid;
-    const int64_t ext[3] = {nx, ny, nz};
+    // a non-periodic axis needs solid end layers (the two layers of that axis only)
     for (int a = 0; a < L.D; ++a) {
         if (P.periodic & (1u << a)) continue;
-        for (int64_t node = 0; node < nn; ++node) {
-            const int64_t r[3] = {node % nx, (node / nx) % ny, node / (nx * ny)};
-            if ((r[a] == 0 || r[a] == ext[a] - 1) && !solid[node]) {
-                delete d;
-                return fail(nullptr, LBM_ERR_ARG, "axis " + std::to_string(a) + " is not periodic but has fluid on an end layer");
+        const int64_t ext[3] = {nx, ny, nz};
+        bool fluid_end = false;
+        for (int64_t z = 0; z < nz && !fluid_end; ++z)
+            for (int64_t y = 0; y < ny && !fluid_end; ++y) {
+                if (a == 0) {
+                    fluid_end = !solid[nx * (y + ny * z)] || !solid[nx - 1 + nx * (y + ny * z)];
+                } else if ((a == 1 && (y == 0 || y == ext[1] - 1)) || (a == 2 && (z == 0 || z == ext[2] - 1))) {
+                    const uint8_t* row = solid + nx * (y + ny * z);
+                    for (int64_t x = 0; x < nx; ++x)
+                        if (!row[x]) { fluid_end = true; break; }
+                }
             }
+        if (fluid_end) {
+            delete d;
+            return fail(nullptr, LBM_ERR_ARG, "axis " + std::to_string(a) + " is not periodic but has fluid on an end layer");
         }
     }
     if (n_cls_ghost != n_ghosts) {
@@ -669,20 +911,31 @@ lbm_status lbm_create_domain(const lbm_params* params, const uint8_t* solid, con
     const bool elements_only = halo_copy && std::strcmp(halo_copy, "elements") == 0;
     d->tma = !elements_only && (P.lattice == 9 ? make_halo_maps<9>(d) : make_halo_maps<19>(d));
     d->tma2 = !elements_only && (P.lattice == 9 ? make_pair_maps<9>(d) : make_pair_maps<19>(d));
-    // upload node classes and the ghost table; the bounce-back mask is built on the device
-    // device node indices use the padded row pitch
-    std::vector<int32_t> gnode(n_ghosts), pcorner(d->h_corner.size());
-    for (int64_t g = 0; g < n_ghosts; ++g) gnode[g] = (int32_t)padded_node(d, ghosts[g].node);
-    for (size_t k = 0; k < pcorner.size(); ++k) pcorner[k] = (int32_t)padded_node(d, d->h_corner[k]);
-    std::vector<uint8_t> pcls((size_t)L.nn, CLS_SOLID);
-    for (int64_t r = 0; r < nn / nx; ++r)                  // row by row: the padding columns stay solid
-        std::memcpy(&pcls[(size_t)(r * L.px)], &d->h_cls[(size_t)(r * nx)], (size_t)nx);
+    // upload the row bit masks (into the staging planes, 2 W bytes per row
+    // against their 8 px) and the ghost table; the node classes and the
+    // bounce-back mask are built from them on the device, with the padded row
+    // pitch of the device fields
     cudaStream_t s = d->stream;
-    if (cudaMemsetAsync(d->ws, 0, L.total, s) != cudaSuccess) return bail("cudaMemset failed");
-    if (cudaMemcpyAsync(d->cls(), pcls.data(), L.nn, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    const size_t bits_bytes = d->fluid_bits.size() * sizeof(uint64_t);
+    uint64_t* dF = d->at<uint64_t>(L.off_stage);
+    uint64_t* dG = dF + d->fluid_bits.size();
+    if (2 * bits_bytes > 2 * (size_t)L.plane * L.elem) return bail("row bit masks do not fit the staging planes");
+    // zero state, except the second population buffers (N(1), B(1), contiguous
+    // before phi): the first step writes every fluid node's slots there before
+    // any read, and no pull reads a non-fluid node's slots
+    if (cudaMemsetAsync(d->ws, 0, L.off_N[1], s) != cudaSuccess ||
+        cudaMemsetAsync(d->ws + L.off_phi, 0, L.total - L.off_phi, s) != cudaSuccess)
+        return bail("cudaMemset failed");
+    if (cudaMemcpyAsync(dF, d->fluid_bits.data(), bits_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dG, d->ghost_bits.data(), bits_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return bail("upload of node classes failed");
-    dispatch(d, [&](auto Lx) { decltype(Lx)::build_mask(d->cfg, d->cls(), d->mask(), s); });
-    if (cudaGetLastError() != cudaSuccess) return bail("launch of the mask kernel failed");
+    dispatch(d, [&](auto Lx) {
+        decltype(Lx)::expand_classes(d->cfg, d->row_words, dF, dG, d->cls(), s);
+        decltype(Lx)::build_mask(d->cfg, d->cls(), d->mask(), s);
+    });
+    if (cudaGetLastError() != cudaSuccess) return bail("launch of the class and mask kernels failed");
+    const std::vector<int32_t>& gnode = d->h_pnode;
+    const std::vector<int32_t>& pcorner = d->h_pcorner;
     if (n_ghosts > 0) {
         if (cudaMemcpyAsync(d->at<void>(L.off_gnode), gnode.data(), n_ghosts * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaMemcpyAsync(d->at<void>(L.off_gcorner), pcorner.data(), pcorner.size() * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -785,7 +1038,7 @@ lbm_status lbm_diagnostics(lbm_domain* d, const lbm_probe* probe, lbm_diag* out)
     double* partial = d->at<double>(L.off_partial);
     double* dout = d->at<double>(L.off_dout);
     dispatch(d, [&](auto Lx) {
-        decltype(Lx)::diag(d->cfg, d->cls(), d->N(d->cur), d->phi(), d->U(d->cur), d->p(), pr, partial, dout,
+        decltype(Lx)::diag(d->cfg, d->mask(), d->N(d->cur), d->phi(), d->U(d->cur), d->p(), pr, partial, dout,
                            d->stream);
     });
     CUDA_TRY(d, cudaGetLastError());
@@ -863,8 +1116,7 @@ lbm_status lbm_read_state(lbm_domain* d, int32_t field, double* host_out) {
             lbm_status s = download(d, out, stage, nn);
             if (s != LBM_OK) return s;
             if (base != 0.0)                       // deviations from the storage reference -> values, in double
-                for (int64_t k = 0; k < nn; ++k)
-                    if (d->h_cls[k] == CLS_FLUID) out[k] += base;
+                for_fluid_nodes(d, [&](int64_t k) { out[k] += base; });
         }
         return LBM_OK;
     }
@@ -922,12 +1174,19 @@ lbm_status lbm_write_state(lbm_domain* d, int32_t field, const double* host_in) 
     }
     case LBM_FIELD_PHI:
         return upload(d, d->phi(), host_in, nn);
-    case LBM_FIELD_U:
+    case LBM_FIELD_U: {
+        // the velocity of a non-fluid node is 0 whatever the caller passes: the
+        // stencils read it there as the wall's velocity
+        std::vector<double> ua((size_t)nn);
         for (int a = 0; a < L.D; ++a) {
-            lbm_status s = upload(d, (char*)d->U(d->cur) + (size_t)a * L.plane * L.elem, host_in + (size_t)a * nn, nn);
+            const double* src = host_in + (size_t)a * nn;
+            std::fill(ua.begin(), ua.end(), 0.0);
+            for_fluid_nodes(d, [&](int64_t k) { ua[k] = src[k]; });
+            lbm_status s = upload(d, (char*)d->U(d->cur) + (size_t)a * L.plane * L.elem, ua.data(), nn);
             if (s != LBM_OK) return s;
         }
         return LBM_OK;
+    }
     case LBM_FIELD_P:
         return upload(d, d->p(), host_in, nn);
     }

@@ -29,6 +29,25 @@ __device__ __forceinline__ int64_t shifted(const Dims& d, int x, int y, int z, i
     return xx + (int64_t)d.px * (yy + (int64_t)d.ny * zz);
 }
 
+// Node classes of the padded grid from the host's row bit masks: rows r =
+// y + ny z of W 64-bit words, bit x of F[r W + x / 64] set for a fluid node,
+// of G for a ghost (a solid node with a fluid stencil neighbour); columns
+// x >= nx are padding, solid.
+static __global__ void k_expand_classes(Dims d, int W, const uint64_t* __restrict__ F, const uint64_t* __restrict__ G,
+                                 uint8_t* __restrict__ cls) {
+    const int nn = (int)padded_nodes(d);
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn; node += gridDim.x * blockDim.x) {
+        const int x = node % d.px, r = node / d.px;
+        uint8_t c = CLS_SOLID;
+        if (x < d.nx) {
+            const int w = r * W + (x >> 6), b = x & 63;
+            if ((F[w] >> b) & 1u) c = CLS_FLUID;
+            else if ((G[w] >> b) & 1u) c = CLS_GHOST;
+        }
+        cls[node] = c;
+    }
+}
+
 // Per-node bounce-back mask from the node classes: bit i (1 <= i < Q) set when
 // x - c_i (periodic wrap) is not a fluid node, MASK_NOT_FLUID for non-fluid x.
 template <int Q>
@@ -95,17 +114,16 @@ __global__ void k_init_pops(Dims d, StepParams<T> P, const uint8_t* __restrict__
                             S* __restrict__ Nst, S* __restrict__ Bst) {
     using L = Lattice<Q>;
     constexpr bool kShift = PopStore<S>::kShift;
-    const int64_t nn = padded_nodes(d);
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
-         node += (int64_t)gridDim.x * blockDim.x) {
+    const int nn = (int)padded_nodes(d);                    // node indices are below 2^31
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn; node += gridDim.x * blockDim.x) {
         if (cls[node] != CLS_FLUID) continue;
-        int x, y, z;
-        node_xyz(node, d, x, y, z);
+        const int x = node % d.px, t = node / d.px, y = t % d.ny, z = t / d.ny;
+        const Wrap W(x, y, z, d.nx, d.ny, d.nz, d.px);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int64_t dn = shifted(d, x, y, z, L::cx(i), L::cy(i), L::cz(i));
+            const int dn = node + W.off(L::cx(i), L::cy(i), L::cz(i));
             const T ph = (cls[dn] == CLS_FLUID) ? phi[dn] : phi[node];
-            const int pl = (int)d.plane, nd = (int)node;
+            const int pl = (int)d.plane, nd = node;
             // deviation storage: N_i - chi_i(stored) = the exact chi_i minus the
             // stored one; B_i - chi_i(stored)/2 = phi (that) + (phi - 1/2) chi_i(stored)
             const T e = P.chi_err[i == 0 ? 0 : (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i) == 1
@@ -175,9 +193,22 @@ struct ProbeDev {
     double center[3], radius, normal[3], exclude;
 };
 
+// The direction index of the lattice vector (dx, dy, dz).
+template <int Q>
+__host__ __device__ constexpr int dir_index(int dx, int dy, int dz) {
+    for (int i = 0; i < Q; ++i)
+        if (Lattice<Q>::cx(i) == dx && Lattice<Q>::cy(i) == dy && Lattice<Q>::cz(i) == dz) return i;
+    return -1;
+}
+
+// Per-node values are computed in the domain's arithmetic type T (the values
+// as stored, summed over the Q pulled populations), the per-thread sums in
+// FP64 and the counts in integers, so a float domain costs a few FP64 adds
+// per node.  Neighbours come from the bounce-back mask and 32-bit periodic
+// offsets (node indices are below 2^31).
 template <int Q, typename T, typename S>
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rho_l, double rho_g,
-                                                               const uint8_t* __restrict__ cls, StepParams<T> P,
+                                                               const uint32_t* __restrict__ mask, StepParams<T> P,
                                                                const S* __restrict__ Nst, const T* __restrict__ phi,
                                                                const T* __restrict__ u, const T* __restrict__ p,
                                                                ProbeDev pr, double* __restrict__ partial) {
@@ -187,57 +218,66 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rh
 #pragma unroll
     for (int k = 0; k < DG_REC; ++k) acc[k] = 0.0;
     acc[DG_APEX] = -INFINITY;
-    const int64_t nn = padded_nodes(d);
+    int n_fluid = 0, n_in = 0, n_out = 0, n_nan = 0, n_iface = 0, n_fit = 0;
+    T max_u2 = T(0);
+    const int nn = (int)padded_nodes(d), pl = (int)d.plane;
     const int n[3] = {d.nx, d.ny, d.nz};
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
-         node += (int64_t)gridDim.x * blockDim.x) {
-        if (cls[node] != CLS_FLUID) continue;
-        int x, y, z;
-        node_xyz(node, d, x, y, z);
-        const double ph = (double)phi[node];
-        acc[DG_NFLUID] += 1.0;
-        acc[DG_PHI] += ph;
-        double ps = 0.0;
+    const T rl = T(rho_l), rg = T(rho_g);
+    // deviation storage: the per-node sum runs over the stored deviations (small
+    // values, little rounding) and the references sum_i chi_i join in FP64
+    double chi_total = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) chi_total += (double)P.chi[i];
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn; node += gridDim.x * blockDim.x) {
+        const uint32_t m = mask[node];
+        if (m & MASK_NOT_FLUID) continue;
+        const int x = node % d.px, t = node / d.px, y = t % d.ny, z = t / d.ny;
+        const Wrap W(x, y, z, d.nx, d.ny, d.nz, d.px);
+        const T ph = phi[node];
+        ++n_fluid;
+        acc[DG_PHI] += (double)ph;
+        // the populations after streaming: pulled from x - c_i, or bounced back
+        T ps = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int64_t sn = shifted(d, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
-            const bool from_fluid = cls[sn] == CLS_FLUID;
-            ps += pop_load<S, double>(Nst, from_fluid ? i : L::opp(i), (int)d.plane, (int)(from_fluid ? sn : node),
-                                      kScaleN) +
-                  (PopStore<S>::kShift ? (double)P.chi[i] : 0.0);
+            const bool from_fluid = i == 0 || !((m >> i) & 1u);
+            const int src = from_fluid ? node + W.off(-L::cx(i), -L::cy(i), -L::cz(i)) : node;
+            ps += pop_load<S, T>(Nst, from_fluid ? i : L::opp(i), pl, src, kScaleN);
         }
-        acc[DG_POP] += ps;
-        double u2 = 0.0;
+        acc[DG_POP] += PopStore<S>::kShift ? (double)ps + chi_total : (double)ps;
+        T u2 = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const double ua = (double)u[a * d.plane + node];
+            const T ua = u[a * pl + node];
             u2 += ua * ua;
         }
-        if (u2 > acc[DG_MAXU2]) acc[DG_MAXU2] = u2;
-        if (!isfinite(u2) || !isfinite(ph)) acc[DG_NAN] += 1.0;     // NaN or +-Inf in phi or u
-        const double phh = (rho_l * ph + rho_g * (1.0 - ph)) * (double)p[node];
-        if (ph > 1.0 - 1e-3) { acc[DG_PIN] += phh; acc[DG_NIN] += 1.0; }
-        if (ph < 1e-3) { acc[DG_POUT] += phh; acc[DG_NOUT] += 1.0; }
+        if (u2 > max_u2) max_u2 = u2;
+        if (!isfinite(u2) || !isfinite(ph)) ++n_nan;                  // NaN or +-Inf in phi or u
+        const T phh = (rl * ph + rg * (T(1) - ph)) * p[node];
+        if (ph > T(1.0 - 1e-3)) { acc[DG_PIN] += (double)phh; ++n_in; }
+        if (ph < T(1e-3)) { acc[DG_POUT] += (double)phh; ++n_out; }
         if (pr.kind == 0) continue;
         const int r[3] = {x, y, z};
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-            const int64_t yn = shifted(d, x, y, z, a == 0, a == 1, a == 2);
-            if (cls[yn] != CLS_FLUID) continue;
-            const double p1 = (double)phi[yn];
-            if ((ph >= 0.5) == (p1 >= 0.5)) continue;
-            const double t = (0.5 - ph) / (p1 - ph);
+            // the +e_a neighbour is x - c_k for c_k = -e_a
+            constexpr int kBack[3] = {dir_index<Q>(-1, 0, 0), dir_index<Q>(0, -1, 0), dir_index<Q>(0, 0, -1)};
+            if ((m >> kBack[a]) & 1u) continue;
+            const int yn = node + W.off(a == 0, a == 1, a == 2);
+            const double phd = (double)ph, p1 = (double)phi[yn];
+            if ((phd >= 0.5) == (p1 >= 0.5)) continue;
+            const double tt = (0.5 - phd) / (p1 - phd);
             double q[3] = {0.0, 0.0, 0.0};
             double q2 = 0.0, h = 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                double v = r[k] + (k == a ? t : 0.0) - pr.center[k];
+                double v = r[k] + (k == a ? tt : 0.0) - pr.center[k];
                 v -= n[k] * floor(v / n[k] + 0.5);
                 q[k] = v;
                 q2 += v * v;
                 h += v * pr.normal[k];
             }
-            acc[DG_NIFACE] += 1.0;
+            ++n_iface;
             if (h > acc[DG_APEX]) acc[DG_APEX] = h;
             const double dist = (pr.kind == 1) ? sqrt(q2) - pr.radius : h;
             if (dist < pr.exclude) continue;
@@ -251,9 +291,16 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rh
                 for (int j = 0; j <= D; ++j) acc[DG_A + 4 * i + j] += row[i] * row[j];
                 acc[DG_B + i] += -q2 * row[i];
             }
-            acc[DG_NFIT] += 1.0;
+            ++n_fit;
         }
     }
+    acc[DG_NFLUID] = n_fluid;
+    acc[DG_NIN] = n_in;
+    acc[DG_NOUT] = n_out;
+    acc[DG_NAN] = n_nan;
+    acc[DG_NIFACE] = n_iface;
+    acc[DG_NFIT] = n_fit;
+    acc[DG_MAXU2] = (double)max_u2;
     // block reduction in a fixed order: warp shuffles, then warps in index order
     __shared__ double s_w[DIAG_THREADS / 32][DG_REC];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

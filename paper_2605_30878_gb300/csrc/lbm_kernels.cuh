@@ -667,19 +667,14 @@ struct FloatNode {
     float shb1, shb2;                          // (phi - 1/2) chi_i per class, in B's units
     float phiB;
 
-    __device__ __forceinline__ void compute(const StepParams<float>& P, const float (&N)[Q], float phi_,
-                                            const float (&gp_)[3], float lap, const float (&gu)[3][3]) {
-        phi = phi_;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gp[a] = gp_[a];
+    // raw moments of the pulled N (storage units): sum, first and second moments
+    float m_sum, m_u0[3], m_xx, m_yy, m_zz, m_xy, m_xz, m_yz;
 
-        // mixture density and viscosity (Sec. II), relaxation time (Appendix A)
-        const float rho = fmaf(P.drho, phi, P.rho_g);
-        const float inv_rho = rcp(rho);
-        const float nu = rcp(fmaf(phi, P.inv_nu_l - P.inv_nu_g, P.inv_nu_g));     // 1 / (phi/nu_l + (1-phi)/nu_g)
-        const float tau = fmaf(3.0f, nu, 0.5f);
-
-        // force-free velocity, moments and the pressure of this step (Eq. pressureUpdate)
+    // The moments need only the pulled populations, not the halo: the two-node
+    // kernel takes them before its barrier, so that the 2 (Q - 1) pulled values
+    // are not held across the stencils.
+    __device__ __forceinline__ void moments(const float (&N)[Q]) {
+        // force-free velocity and the moments of Eq. (pressureUpdate) and the collision
         Acc u0s[3], sm, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
@@ -698,6 +693,32 @@ struct FloatNode {
             Pxz.add(cx * cz, sp);
             Pyz.add(cy * cz, sp);
         }
+        m_sum = sm.get();
+#pragma unroll
+        for (int a = 0; a < 3; ++a) m_u0[a] = u0s[a].get();
+        m_xx = Pxx.get(); m_yy = Pyy.get(); m_zz = Pzz.get();
+        m_xy = Pxy.get(); m_xz = Pxz.get(); m_yz = Pyz.get();
+    }
+
+    __device__ __forceinline__ void compute(const StepParams<float>& P, const float (&N)[Q], float phi_,
+                                            const float (&gp_)[3], float lap, const float (&gu)[3][3]) {
+        moments(N);
+        compute(P, phi_, gp_, lap, gu);
+    }
+
+    // the rest of the node update, after moments()
+    __device__ __forceinline__ void compute(const StepParams<float>& P, float phi_, const float (&gp_)[3], float lap,
+                                            const float (&gu)[3][3]) {
+        phi = phi_;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gp[a] = gp_[a];
+
+        // mixture density and viscosity (Sec. II), relaxation time (Appendix A)
+        const float rho = fmaf(P.drho, phi, P.rho_g);
+        const float inv_rho = rcp(rho);
+        const float nu = rcp(fmaf(phi, P.inv_nu_l - P.inv_nu_g, P.inv_nu_g));     // 1 / (phi/nu_l + (1-phi)/nu_g)
+        const float tau = fmaf(3.0f, nu, 0.5f);
+
         // FP16 storage: N came in storage units (times sN = 2^16); the moments are
         // linear in N, so the scale is taken out where each is used (exactly, a
         // power of two): here for u0 and the pressure, in the stress projections
@@ -705,14 +726,14 @@ struct FloatNode {
         constexpr float r = 1.0f / sN;
         float u0[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u0[a] = (a < D) ? (UNITS ? u0s[a].get() * r : u0s[a].get()) : 0.f;
+        for (int a = 0; a < 3; ++a) u0[a] = (a < D) ? (UNITS ? m_u0[a] * r : m_u0[a]) : 0.f;
         // Eq. (pressureUpdate) takes sum_{i>0} N_i - (1 - chi_0) with the exact
         // chi; the deviations are stored from the rounded chi of the storage, whose
         // moving values sum to 1 - chi[0], so the difference of the two is
         // chi_0 - chi[0], the rest class's correction (without it the float
         // pressure would sit a constant ~4e-8 off, which F_p = -p grad(rho)
         // turns into a velocity error at a density contrast)
-        const float pres_base = (UNITS ? fmaf(sm.get(), r, P.chi_err[0]) : sm.get() + P.chi_err[0]) *
+        const float pres_base = (UNITS ? fmaf(m_sum, r, P.chi_err[0]) : m_sum + P.chi_err[0]) *
                                 float(1.0 / 3.0);
         const float inv_1mw0 = float(1.0 / (1.0 - w0));
 
@@ -755,7 +776,7 @@ struct FloatNode {
         // in N's storage units (the moments are raw, the u u terms take the scale)
         const float omega1 = 1.0f - rcp(tau);                                       // 1 - s_nu
         const float o4 = omega1 * 0.25f;
-        const float pxx = Pxx.get(), pyy = Pyy.get();
+        const float pxx = m_xx, pyy = m_yy;
         // (these products enter the direction sums: __fmul_rn keeps the compiler
         // from fusing them there in one kernel and not in another)
         base0 = __fmul_rn(3.0f, u[0]);
@@ -764,18 +785,18 @@ struct FloatNode {
         if (D == 2) {
             A0 = __fmul_rn(o4, fmaf(-sN, fmaf(u[0], u[0], -(u[1] * u[1])), pxx - pyy));     // m7 . f / |m7|^2
             A1 = 0.f;
-            Axy = __fmul_rn(o4, fmaf(-sN * u[0], u[1], Pxy.get()));                      // m8 . f / |m8|^2
+            Axy = __fmul_rn(o4, fmaf(-sN * u[0], u[1], m_xy));                      // m8 . f / |m8|^2
             Axz = Ayz = 0.f;
         } else {
-            const float pzz = Pzz.get();
+            const float pzz = m_zz;
             // 2 ux^2 - uy^2 - uz^2 = 3 ux^2 - u.u
             A0 = __fmul_rn(omega1 * float(1.0 / 36.0),
                            fmaf(-sN, fmaf(base0, u[0], -uu), fmaf(2.0f, pxx, -pyy) - pzz));
             A1 = __fmul_rn(omega1 * float(1.0 / 12.0), fmaf(-sN, fmaf(u[1], u[1], -(u[2] * u[2])), pyy - pzz));
             const float su0 = -sN * u[0];
-            Axy = __fmul_rn(o4, fmaf(su0, u[1], Pxy.get()));
-            Axz = __fmul_rn(o4, fmaf(su0, u[2], Pxz.get()));
-            Ayz = __fmul_rn(o4, fmaf(-sN * u[1], u[2], Pyz.get()));
+            Axy = __fmul_rn(o4, fmaf(su0, u[1], m_xy));
+            Axz = __fmul_rn(o4, fmaf(su0, u[2], m_xz));
+            Ayz = __fmul_rn(o4, fmaf(-sN * u[1], u[2], m_yz));
         }
 
         // segregation: n_phi = grad phi / max(|grad phi|, 1e-6)

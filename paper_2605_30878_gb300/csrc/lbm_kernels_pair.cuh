@@ -41,10 +41,13 @@ struct PairTile {
 };
 
 // Resident blocks per SM the pair kernel is compiled for (registers per
-// thread <= 65536 / (THREADS * blocks)): 6 (80 registers) measured as fast
-// as 5 in FP32 and 2% faster with FP16 storage; 4 is 20% slower, 7 and 8
-// spill 68 bytes or more.
-constexpr int kPairBlocks = 6;
+// thread <= 65536 / (THREADS * blocks)), measured at 192^3: FP32 storage runs
+// best at 6 (80 registers; 7 blocks at 72 registers spill 20 bytes and run 4%
+// slower), FP16 storage at 7 (3% faster than 6: its bytes per node are fewer,
+// so more warps in flight pay for the spill); 4 is 20% slower, 8 spills 76
+// bytes or more.
+template <typename S> struct PairBlocks { static constexpr int value = 6; };
+template <> struct PairBlocks<__half> { static constexpr int value = 7; };
 
 // The values at halo slots hc + o and hc + o + 1 (hc even): one aligned
 // two-wide load for even o, else the odd half of the pair below and the even
@@ -124,6 +127,11 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
                     NB[i] = (float)PS::load_units(mv, idx_checked((L::opp(i) - 1) * pl + nodeA + 1, nmv, err));
         }
     }
+    // the moments of both nodes while the halo copy completes; the pulled
+    // values are then dead, which keeps them out of the registers the stencils need
+    FloatNode<Q, kUnits, CONTRAST> nA, nB;
+    nA.moments(NA);
+    nB.moments(NB);
     const bool halo_ok = halo_complete<Tl, float, S>(b, interior, bar, s_phi, s_u, fix_v, fix_at);
     __syncthreads();
     if (!(fluidA || fluidB) || !halo_ok) return;
@@ -160,9 +168,8 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
             }
         }
     }
-    FloatNode<Q, kUnits, CONTRAST> nA, nB;
-    nA.compute(P, NA, ph.x, gA, lA, dA);
-    nB.compute(P, NB, ph.y, gB, lB, dB);
+    nA.compute(P, ph.x, gA, lA, dA);
+    nB.compute(P, ph.y, gB, lB, dB);
 
     // u and p of the pair in one store per field; 0 at a node that is not fluid
     // (the velocity halo reads 0 at solid nodes)
@@ -203,7 +210,7 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
 }
 
 template <int Q, typename S, bool CONTRAST>
-__global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
+__global__ void __launch_bounds__(PairTile<Q>::THREADS, PairBlocks<S>::value)
     k_step_pair(StepParams<float> P, StepBuffers<float, S> b, const __grid_constant__ CUtensorMap tm_phi,
                 const __grid_constant__ CUtensorMap tm_u, int tma) {
     using Tl = PairTile<Q>;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
 // Batched form: one pair tile of one domain per block, the domain's
 // parameters in its constant-memory slot (as k_step_batched, tile shape 5).
 template <int Q, typename S, bool CONTRAST>
-__global__ void __launch_bounds__(PairTile<Q>::THREADS, kPairBlocks)
+__global__ void __launch_bounds__(PairTile<Q>::THREADS, PairBlocks<S>::value)
     k_step_pair_batched(const int4* __restrict__ tiles, const CUtensorMap* __restrict__ maps, int parity) {
     using Tl = PairTile<Q>;
     constexpr int D = Tl::D;

@@ -68,6 +68,8 @@ struct Launch {
                          double ghost_value, cudaStream_t s);
     static void init_pops(const StepConfig& c, const uint8_t* cls, const void* phi, void* N, void* B, cudaStream_t s);
     static void build_mask(const StepConfig& c, const uint8_t* cls, uint32_t* mask, cudaStream_t s);
+    static void expand_classes(const StepConfig& c, int W, const uint64_t* F, const uint64_t* G, uint8_t* cls,
+                               cudaStream_t s);
     // base subtracted from direction i of N (is_b = false) or B (true) in
     // storage; scatter_dir takes and gather_dir returns the values less this
     // base (the host adds and subtracts it in double, so a float domain's
@@ -95,7 +97,7 @@ struct Launch {
     static void fill_ghost_table(void* out, int64_t n, const int32_t* node, const int32_t* corner, const void* wt,
                                  double exp_eps, double eps, void* phi, int rule, int64_t plane, int* err);
     static int diag_blocks(const Dims& d);
-    static void diag(const StepConfig& c, const uint8_t* cls, const void* Nst, const void* phi, const void* u,
+    static void diag(const StepConfig& c, const uint32_t* mask, const void* Nst, const void* phi, const void* u,
                      const void* p, const ProbeDev& pr, double* partial, double* out, cudaStream_t s);
 };
 

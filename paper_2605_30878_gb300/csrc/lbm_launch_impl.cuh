@@ -166,6 +166,12 @@ void Launch<T, S>::init_pops(const StepConfig& c, const uint8_t* cls, const void
 }
 
 template <typename T, typename S>
+void Launch<T, S>::expand_classes(const StepConfig& c, int W, const uint64_t* F, const uint64_t* G, uint8_t* cls,
+                                  cudaStream_t s) {
+    k_expand_classes<<<flat_blocks(c.d), 256, 0, s>>>(c.d, W, F, G, cls);
+}
+
+template <typename T, typename S>
 void Launch<T, S>::build_mask(const StepConfig& c, const uint8_t* cls, uint32_t* mask, cudaStream_t s) {
     if (c.Q == 9)
         k_build_mask<9><<<flat_blocks(c.d), 256, 0, s>>>(c.d, cls, mask);
@@ -304,15 +310,15 @@ int Launch<T, S>::diag_blocks(const Dims& d) {
 }
 
 template <typename T, typename S>
-void Launch<T, S>::diag(const StepConfig& c, const uint8_t* cls, const void* Nst, const void* phi, const void* u,
+void Launch<T, S>::diag(const StepConfig& c, const uint32_t* mask, const void* Nst, const void* phi, const void* u,
                  const void* p, const ProbeDev& pr, double* partial, double* out, cudaStream_t s) {
     const int nb = diag_blocks(c.d);
     const StepParams<T> P = params(c);
     if (c.Q == 9)
-        k_diag_partial<9, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, P, (const S*)Nst,
+        k_diag_partial<9, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, mask, P, (const S*)Nst,
                                                             (const T*)phi, (const T*)u, (const T*)p, pr, partial);
     else
-        k_diag_partial<19, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, cls, P, (const S*)Nst,
+        k_diag_partial<19, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, mask, P, (const S*)Nst,
                                                              (const T*)phi, (const T*)u, (const T*)p, pr, partial);
     k_diag_final<<<1, 32, 0, s>>>(nb, partial, out);
 }
