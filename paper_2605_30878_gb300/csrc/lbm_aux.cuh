@@ -80,14 +80,16 @@ __global__ void k_build_mask(Dims d, const uint8_t* __restrict__ cls, uint32_t* 
 template <int D, typename T>
 __global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restrict__ phi, int mode, double cx,
                            double cy, double cz, double R0, double W, double ghost_value) {
-    const int64_t nn = padded_nodes(d);
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < nn;
-         node += (int64_t)gridDim.x * blockDim.x) {
+    // more than 10 W from the interface, |2 (R0 - r) / W| >= 20 and
+    // 1 - |tanh| < 1e-17: the profile is 0 or 1 to double precision there, so
+    // tanh (slow on this GPU's few FP64 units) runs only inside that band
+    const double far = 10.0 * W, out2 = (R0 + far) * (R0 + far), in2 = R0 > far ? (R0 - far) * (R0 - far) : -1.0;
+    const int nn = (int)padded_nodes(d);                    // node indices are below 2^31
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn; node += gridDim.x * blockDim.x) {
         const uint8_t c = cls[node];
         if (c == CLS_FLUID) {
             if (mode == 0) {
-                int x, y, z;
-                node_xyz(node, d, x, y, z);
+                const int x = node % d.px, t = node / d.px, y = t % d.ny, z = t / d.ny;
                 const double ctr[3] = {cx, cy, cz};
                 const int n[3] = {d.nx, d.ny, d.nz};
                 const int r[3] = {x, y, z};
@@ -95,10 +97,14 @@ __global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restric
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     double v = r[a] - ctr[a];
-                    if (d.periodic & (1u << a)) v -= n[a] * floor(v / n[a] + 0.5);
+                    // nearest periodic image; the divide only where one is needed
+                    if ((d.periodic & (1u << a)) && (v > 0.5 * n[a] || v < -0.5 * n[a]))
+                        v -= n[a] * floor(v / n[a] + 0.5);
                     d2 += v * v;
                 }
-                phi[node] = (T)(0.5 * (1.0 + tanh(2.0 * (R0 - sqrt(d2)) / W)));
+                phi[node] = d2 >= out2 ? T(0)
+                          : d2 <= in2  ? T(1)
+                                       : (T)(0.5 * (1.0 + tanh(2.0 * (R0 - sqrt(d2)) / W)));
             }
         } else {
             phi[node] = (c == CLS_GHOST) ? (T)ghost_value : T(0);
@@ -322,12 +328,27 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_partial(Dims d, double rh
     }
 }
 
-static __global__ void k_diag_final(int nblocks, const double* __restrict__ partial, double* __restrict__ out) {
-    const int k = threadIdx.x;
-    if (k >= DG_REC) return;
-    double v = partial[k];
-    for (int b = 1; b < nblocks; ++b) v = (k >= DG_MAXU2) ? fmax(v, partial[b * DG_REC + k]) : v + partial[b * DG_REC + k];
-    out[k] = v;
+// The per-block records summed in a fixed order: thread (j, k) of the
+// 32 x 32 block sums entry k of blocks j, j + 32, j + 64, ..., then entry k's
+// 32 partial sums are added in j order (32 loads in flight per entry instead
+// of one after the other).
+static __global__ void __launch_bounds__(1024) k_diag_final(int nblocks, const double* __restrict__ partial,
+                                                            double* __restrict__ out) {
+    __shared__ double s[32][DG_REC];
+    const int k = threadIdx.x, j = threadIdx.y;
+    const bool is_max = k >= DG_MAXU2;
+    double v = is_max ? -INFINITY : 0.0;
+    for (int b = j; b < nblocks; b += 32) {
+        const double w = partial[b * DG_REC + k];
+        v = is_max ? fmax(v, w) : v + w;
+    }
+    s[j][k] = v;
+    __syncthreads();
+    if (j == 0) {
+        double r = s[0][k];
+        for (int jj = 1; jj < 32; ++jj) r = is_max ? fmax(r, s[jj][k]) : r + s[jj][k];
+        out[k] = r;
+    }
 }
 
 }  // namespace lbmgpu

@@ -320,7 +320,7 @@ void Launch<T, S>::diag(const StepConfig& c, const uint32_t* mask, const void* N
     else
         k_diag_partial<19, T, S><<<nb, DIAG_THREADS, 0, s>>>(c.d, c.rho_l, c.rho_g, mask, P, (const S*)Nst,
                                                              (const T*)phi, (const T*)u, (const T*)p, pr, partial);
-    k_diag_final<<<1, 32, 0, s>>>(nb, partial, out);
+    k_diag_final<<<1, dim3(DG_REC, 32), 0, s>>>(nb, partial, out);
 }
 
 }  // namespace lbmgpu
