@@ -9,7 +9,7 @@ kernel, color kernel) over the whole grid.  MLUPS counts every node of the grid
 (solid included), as the paper's Eq. (MLUPSDefinition).
 
 Further objects of the same JSON line (rank 0, one GPU): the same case over
-its five contact angles, FP32 against FP64 after 400 steps and FP32 on to 2000
+its five contact angles, FP32 against FP64 after 400 steps and FP32 on to 20000
 (`theta_sweep`); the other population storage on the same case; the 64
 batched cases; the paper's Table I grids; the 256^3 sphere-packing
 imbibition, FP32 and FP16 storage against an FP64 reference (`packing`); the
@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-other-storage", action="store_true",
                     help="skip the run of the same case with the other population storage (fp16 / fp32)")
     ap.add_argument("--table-steps", type=int, default=2000)
-    ap.add_argument("--sweep-steps", type=int, default=2000,
+    ap.add_argument("--sweep-steps", type=int, default=20000,
                     help="contact-angle sweep 30..150 deg of the bench case for this many FP32 steps (0 skips it)")
     ap.add_argument("--sweep-fp64-steps", type=int, default=400,
                     help="steps of the FP32-vs-FP64 comparison within the sweep (and of the bench line's "

@@ -15,6 +15,8 @@
 #include <thread>
 #include <vector>
 
+#include <unistd.h>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -161,7 +163,16 @@ namespace {
 class HostPool {
 public:
     static HostPool& get() {
-        static HostPool* pool = new HostPool();
+        // a forked child inherits none of the threads, and perhaps a mutex some
+        // thread held at the fork: it gets a pool of its own
+        static std::mutex make;
+        static HostPool* pool = nullptr;
+        static pid_t owner = 0;
+        std::lock_guard<std::mutex> lk(make);
+        if (!pool || owner != getpid()) {
+            pool = new HostPool();
+            owner = getpid();
+        }
         return *pool;
     }
     int threads() const { return workers_ + 1; }

@@ -55,6 +55,7 @@ def params(q, nx, ny, nz):
 CASES = [
     (9, 63, 17, 1), (9, 64, 9, 1), (9, 65, 5, 1), (9, 130, 3, 1), (9, 7, 1, 1),
     (19, 63, 5, 4), (19, 64, 3, 3), (19, 65, 4, 2), (19, 129, 2, 1), (19, 8, 1, 5), (19, 1, 6, 6),
+    (19, 130, 130, 130), (9, 2000, 1500, 1),      # large enough to be split over the host thread pool
 ]
 
 
@@ -96,3 +97,57 @@ def test_ghost_classes_match_brute_force(q, nx, ny, nz):
         with pytest.raises(lbm.LbmError) as e:
             lbm.Domain(P, s8, (dup, normals), workspace="library", stream=0)
         assert "listed twice" in str(e.value), str(e.value)
+
+
+def _validation_error(q=19, nx=130, ny=130, nz=130, seed=0):
+    rng = np.random.default_rng(seed)
+    solid = rng.random((nz, ny, nx)) < 0.5
+    nodes = np.flatnonzero(brute_ghosts(solid, q).reshape(-1))
+    normals = np.zeros((len(nodes), 3))
+    normals[:, 0] = 1.0
+    normals[-1] = (2.0, 0.0, 0.0)
+    try:
+        lbm.Domain(params(q, nx, ny, nz), solid.astype(np.uint8), (nodes, normals), workspace="library", stream=0)
+    except lbm.LbmError as e:
+        return str(e), len(nodes)
+    return "no error", len(nodes)
+
+
+def test_concurrent_creations_share_the_host_pool():
+    """Creation's host work runs on a shared thread pool (these 2.2M-node
+    grids are split over it); calls from several host threads at once are
+    serialised on it and each gets its own answer."""
+    import threading
+    out = {}
+
+    def worker(k):
+        out[k] = [_validation_error(seed=k)[0] for _ in range(10)]
+
+    th = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=60)
+    assert len(out) == 4
+    for k in range(4):
+        msg, n = _validation_error(seed=k)
+        assert all(m == msg for m in out[k]) and ("ghost %d normal" % (n - 1)) in msg
+
+
+def _child(q):
+    q.put(_validation_error()[0])
+
+
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")
+def test_forked_child_gets_its_own_pool():
+    """A child forked after the pool started has none of its threads; its
+    creation calls still finish (on a pool of its own)."""
+    import multiprocessing as mp
+    _validation_error()                        # the parent's pool exists
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    p = ctx.Process(target=_child, args=(q,))
+    p.start()
+    p.join(timeout=60)
+    assert p.exitcode == 0
+    assert "normal is not a unit vector" in q.get(timeout=5)
