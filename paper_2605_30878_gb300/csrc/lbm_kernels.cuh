@@ -620,36 +620,105 @@ __device__ __forceinline__ void pull_bounce_back(const StepParams<T>& P, const S
                                                                     (long long)(Q - 1) * pl, err));
 }
 
+// Value types of the float node update.  SF is a float whose every
+// operation is rounded on its own (round to nearest, never fused unless
+// written as fma): the one-node kernels' type.  F2 holds the same value for
+// two nodes in one 64-bit register pair and operates on both lanes with one
+// packed instruction (PTX add/sub/mul/fma .rn .f32x2, sm_100 and later):
+// the two-node kernel's type.  Each packed lane rounds exactly as the SF
+// operation does, so one source of the update gives both kernels the same
+// results to the bit, and the two-node kernel issues one float instruction
+// where the one-node kernel issues two.
+struct SF {
+    float v;
+    __device__ __forceinline__ SF() {}
+    __device__ __forceinline__ SF(float x) : v(x) {}
+};
+__device__ __forceinline__ SF operator+(SF a, SF b) { return SF(__fadd_rn(a.v, b.v)); }
+__device__ __forceinline__ SF operator-(SF a, SF b) { return SF(__fsub_rn(a.v, b.v)); }
+__device__ __forceinline__ SF operator*(SF a, SF b) { return SF(__fmul_rn(a.v, b.v)); }
+__device__ __forceinline__ SF operator-(SF a) { return SF(-a.v); }
+__device__ __forceinline__ SF fma(SF a, SF b, SF c) { return SF(fmaf(a.v, b.v, c.v)); }
+__device__ __forceinline__ SF rcp(SF a) { return SF(rcp(a.v)); }
+__device__ __forceinline__ SF inv_norm_floor(SF g2, float floor) { return SF(inv_norm_floor(g2.v, floor)); }
+
+struct F2 {
+    unsigned long long v;                       // lane 0 (node A) low, lane 1 (node B) high
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float a) { asm("mov.b64 %0, {%1, %1};" : "=l"(v) : "f"(a)); }
+    __device__ __forceinline__ F2(float a, float b) { asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(a), "f"(b)); }
+    __device__ __forceinline__ float lo() const {
+        float a, b;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+        return a;
+    }
+    __device__ __forceinline__ float hi() const {
+        float a, b;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+        return b;
+    }
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+// -x exactly (sign flip, zeros included), as the scalar negation
+__device__ __forceinline__ F2 operator-(F2 a) { return a * F2(-1.0f); }
+__device__ __forceinline__ F2 rcp(F2 a) { return F2(rcp(a.lo()), rcp(a.hi())); }
+__device__ __forceinline__ F2 inv_norm_floor(F2 g2, float floor) {
+    return F2(inv_norm_floor(g2.lo(), floor), inv_norm_floor(g2.hi(), floor));
+}
+
 // a + k t for an integer coefficient k that is a constant once the direction
 // loops are unrolled: k = 0 emits nothing, k = +/-1 no multiply, and the first
 // term is taken as it is rather than added to a zero (IEEE addition of +0 is
 // not the identity for -0, so the compiler keeps such adds).  The value is the
 // sum the same terms give in the same order, started from zero.
+template <typename V>
 struct Acc {
-    float v = 0.f;
+    V v = V(0.f);
     bool set = false;
-    __device__ __forceinline__ void add(int k, float t) {
+    __device__ __forceinline__ void add(int k, V t) {
         if (k == 0) return;
-        const float kt = k == 1 ? t : (k == -1 ? -t : float(k) * t);
-        v = set ? v + kt : kt;
+        if (!set) {
+            v = k == 1 ? t : (k == -1 ? -t : V(float(k)) * t);
+        } else {
+            v = k == 1 ? v + t : (k == -1 ? v - t : fma(V(float(k)), t, v));
+        }
         set = true;
     }
-    __device__ __forceinline__ float get() const { return set ? v : 0.f; }
+    __device__ __forceinline__ V get() const { return set ? v : V(0.f); }
 };
 
 // ---------------------------------------------------------------------------
-// Float arithmetic of one fluid node, shared by the one-node step kernel and
-// the two-node (pair) kernel, so that both round alike.  Inputs: the pulled
-// populations N (deviations, in storage units with FP16 storage), the color
-// phi at the node and its isotropic stencils gp = grad phi, lap = lap phi and
-// gu[a][b] = d_a u_b (the stencil weights carry the 3 and the 6).
+// Float arithmetic of one fluid node (V = SF), or of the two nodes of a pair
+// (V = F2, one packed lane each), written once so that the one-node and the
+// two-node kernels round alike.  Inputs: the pulled populations N
+// (deviations, in storage units with FP16 storage), the color phi at the node
+// and its isotropic stencils gp = grad phi, lap = lap phi and gu[a][b] = d_a u_b
+// (the stencil weights carry the 3 and the 6).
 //
-// Every sum of two products is written as an explicit fmaf (and every other
-// product feeding an add has one use), so that the compiler has no choice of
-// which product to fuse: kernels that inline this code round alike, whatever
-// else they compute around it.
+// Every operation of V rounds on its own and fuses only where written as fma,
+// so the compiler has no choice of what to fuse: every kernel that inlines
+// this code computes the same values.
 // ---------------------------------------------------------------------------
-template <int Q, bool UNITS, bool CONTRAST>
+template <int Q, bool UNITS, bool CONTRAST, typename V>
 struct FloatNode {
     using L = Lattice<Q>;
     static constexpr int D = L::D;
@@ -659,29 +728,29 @@ struct FloatNode {
     // (the stress projections, the weights, phi, kseg) and the scaled values
     // round exactly as the unscaled ones would.
     static constexpr float sN = UNITS ? kScaleN : 1.0f, sB = UNITS ? kScaleB : 1.0f;
-    float phi, u[3], uu, p;
-    float F[3], gp[3];
-    float A0, A1, Axy, Axz, Ayz;               // stress projections of N - Neq, times (1 - 1/tau)
-    float base0, base1, base2, three_p, halfF;
-    float common1, common2, krc1, krc2;        // per direction class (1 axis, 2 diagonal/edge)
-    float shb1, shb2;                          // (phi - 1/2) chi_i per class, in B's units
-    float phiB;
+    V phi, u[3], uu, p;
+    V F[3], gp[3];
+    V A0, A1, Axy, Axz, Ayz;                   // stress projections of N - Neq, times (1 - 1/tau)
+    V base0, base1, base2, three_p, halfF;
+    V common1, common2, krc1, krc2;            // per direction class (1 axis, 2 diagonal/edge)
+    V shb1, shb2;                              // (phi - 1/2) chi_i per class, in B's units
+    V phiB;
 
     // raw moments of the pulled N (storage units): sum, first and second moments
-    float m_sum, m_u0[3], m_xx, m_yy, m_zz, m_xy, m_xz, m_yz;
+    V m_sum, m_u0[3], m_xx, m_yy, m_zz, m_xy, m_xz, m_yz;
 
     // The moments need only the pulled populations, not the halo: the two-node
-    // kernel takes them before its barrier, so that the 2 (Q - 1) pulled values
-    // are not held across the stencils.
-    __device__ __forceinline__ void moments(const float (&N)[Q]) {
+    // kernel takes them before its barrier, so that the pulled values are not
+    // held across the stencils.
+    __device__ __forceinline__ void moments(const V (&N)[Q]) {
         // force-free velocity and the moments of Eq. (pressureUpdate) and the collision
-        Acc u0s[3], sm, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
+        Acc<V> u0s[3], sm, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
             // odd moments from N_i - N_opp, even ones from N_i + N_opp
             if (L::opp(i) < i) continue;
-            const float sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
+            const V sp = N[i] + N[L::opp(i)], dp = N[i] - N[L::opp(i)];
             sm.add(1, sp);
             u0s[0].add(cx, dp);
             u0s[1].add(cy, dp);
@@ -700,139 +769,132 @@ struct FloatNode {
         m_xy = Pxy.get(); m_xz = Pxz.get(); m_yz = Pyz.get();
     }
 
-    __device__ __forceinline__ void compute(const StepParams<float>& P, const float (&N)[Q], float phi_,
-                                            const float (&gp_)[3], float lap, const float (&gu)[3][3]) {
+    __device__ __forceinline__ void compute(const StepParams<float>& P, const V (&N)[Q], V phi_, const V (&gp_)[3],
+                                            V lap, const V (&gu)[3][3]) {
         moments(N);
         compute(P, phi_, gp_, lap, gu);
     }
 
     // the rest of the node update, after moments()
-    __device__ __forceinline__ void compute(const StepParams<float>& P, float phi_, const float (&gp_)[3], float lap,
-                                            const float (&gu)[3][3]) {
+    __device__ __forceinline__ void compute(const StepParams<float>& P, V phi_, const V (&gp_)[3], V lap,
+                                            const V (&gu)[3][3]) {
         phi = phi_;
 #pragma unroll
         for (int a = 0; a < 3; ++a) gp[a] = gp_[a];
 
         // mixture density and viscosity (Sec. II), relaxation time (Appendix A)
-        const float rho = fmaf(P.drho, phi, P.rho_g);
-        const float inv_rho = rcp(rho);
-        const float nu = rcp(fmaf(phi, P.inv_nu_l - P.inv_nu_g, P.inv_nu_g));     // 1 / (phi/nu_l + (1-phi)/nu_g)
-        const float tau = fmaf(3.0f, nu, 0.5f);
+        const V rho = fma(V(P.drho), phi, V(P.rho_g));
+        const V inv_rho = rcp(rho);
+        const V nu = rcp(fma(phi, V(P.inv_nu_l - P.inv_nu_g), V(P.inv_nu_g)));   // 1 / (phi/nu_l + (1-phi)/nu_g)
+        const V tau = fma(V(3.0f), nu, V(0.5f));
 
         // FP16 storage: N came in storage units (times sN = 2^16); the moments are
         // linear in N, so the scale is taken out where each is used (exactly, a
         // power of two): here for u0 and the pressure, in the stress projections
         // below for the second moments
         constexpr float r = 1.0f / sN;
-        float u0[3];
+        V u0[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u0[a] = (a < D) ? (UNITS ? m_u0[a] * r : m_u0[a]) : 0.f;
+        for (int a = 0; a < 3; ++a) u0[a] = (a < D) ? (UNITS ? m_u0[a] * V(r) : m_u0[a]) : V(0.f);
         // Eq. (pressureUpdate) takes sum_{i>0} N_i - (1 - chi_0) with the exact
         // chi; the deviations are stored from the rounded chi of the storage, whose
         // moving values sum to 1 - chi[0], so the difference of the two is
         // chi_0 - chi[0], the rest class's correction (without it the float
         // pressure would sit a constant ~4e-8 off, which F_p = -p grad(rho)
         // turns into a velocity error at a density contrast)
-        const float pres_base = (UNITS ? fmaf(m_sum, r, P.chi_err[0]) : m_sum + P.chi_err[0]) *
-                                float(1.0 / 3.0);
-        const float inv_1mw0 = float(1.0 / (1.0 - w0));
+        const V pres_base = (UNITS ? fma(m_sum, V(r), V(P.chi_err[0])) : m_sum + V(P.chi_err[0])) *
+                            V(float(1.0 / 3.0));
+        const V inv_1mw0 = V(float(1.0 / (1.0 - w0)));
 
         // forces: surface tension and body force, then (density contrast) the
         // pressure and viscous corrections
-        const float muc = fmaf(P.k3W2, lap, P.k48W * phi * (1.0f - phi) * (phi - 0.5f));   // chemical potential / sigma
-        const float smu = -P.sigma * muc;
+        const V muc = fma(V(P.k3W2), lap, V(P.k48W) * phi * (V(1.0f) - phi) * (phi - V(0.5f)));   // chemical potential / sigma
+        const V smu = V(-P.sigma) * muc;
 #pragma unroll
-        for (int a = 0; a < D; ++a) F[a] = fmaf(smu, gp[a], rho * P.g[a]);
-        if (D == 2) F[2] = 0.f;
+        for (int a = 0; a < D; ++a) F[a] = fma(smu, gp[a], rho * V(P.g[a]));
+        if (D == 2) F[2] = V(0.f);
         if (CONTRAST) {
             // F_p = -p0 grad(rho), F_v = nu (grad u + grad u^T) . grad(rho), grad(rho) = drho grad(phi)
-            const float uu0 = D == 2 ? fmaf(u0[0], u0[0], u0[1] * u0[1])
-                                     : fmaf(u0[0], u0[0], fmaf(u0[1], u0[1], u0[2] * u0[2]));
-            const float p0 = fmaf(-float(0.5 * w0), uu0, pres_base) * inv_1mw0;
-            const float kd = (tau - 0.5f) * float(1.0 / 3.0) * P.drho, pd = -p0 * P.drho;
-            float sv[3];
+            const V uu0 = D == 2 ? fma(u0[0], u0[0], u0[1] * u0[1])
+                                 : fma(u0[0], u0[0], fma(u0[1], u0[1], u0[2] * u0[2]));
+            const V p0 = fma(V(-float(0.5 * w0)), uu0, pres_base) * inv_1mw0;
+            const V kd = (tau - V(0.5f)) * V(float(1.0 / 3.0)) * V(P.drho), pd = -p0 * V(P.drho);
+            V sv[3];
             if (D == 2) {
-                const float t01 = gu[0][1] + gu[1][0];
-                sv[0] = fmaf(t01, gp[1], (gu[0][0] + gu[0][0]) * gp[0]);
-                sv[1] = fmaf(t01, gp[0], (gu[1][1] + gu[1][1]) * gp[1]);
+                const V t01 = gu[0][1] + gu[1][0];
+                sv[0] = fma(t01, gp[1], (gu[0][0] + gu[0][0]) * gp[0]);
+                sv[1] = fma(t01, gp[0], (gu[1][1] + gu[1][1]) * gp[1]);
             } else {
-                const float t01 = gu[0][1] + gu[1][0], t02 = gu[0][2] + gu[2][0], t12 = gu[1][2] + gu[2][1];
-                sv[0] = fmaf(t02, gp[2], fmaf(t01, gp[1], (gu[0][0] + gu[0][0]) * gp[0]));
-                sv[1] = fmaf(t12, gp[2], fmaf(t01, gp[0], (gu[1][1] + gu[1][1]) * gp[1]));
-                sv[2] = fmaf(t12, gp[1], fmaf(t02, gp[0], (gu[2][2] + gu[2][2]) * gp[2]));
+                const V t01 = gu[0][1] + gu[1][0], t02 = gu[0][2] + gu[2][0], t12 = gu[1][2] + gu[2][1];
+                sv[0] = fma(t02, gp[2], fma(t01, gp[1], (gu[0][0] + gu[0][0]) * gp[0]));
+                sv[1] = fma(t12, gp[2], fma(t01, gp[0], (gu[1][1] + gu[1][1]) * gp[1]));
+                sv[2] = fma(t12, gp[1], fma(t02, gp[0], (gu[2][2] + gu[2][2]) * gp[2]));
             }
 #pragma unroll
-            for (int a = 0; a < D; ++a) F[a] = fmaf(kd, sv[a], fmaf(pd, gp[a], F[a]));
+            for (int a = 0; a < D; ++a) F[a] = fma(kd, sv[a], fma(pd, gp[a], F[a]));
         }
 
         // Eq. (velUpdate), Eq. (pressureUpdate)
-        const float hr = 0.5f * inv_rho;
+        const V hr = V(0.5f) * inv_rho;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u[a] = (a < D) ? fmaf(F[a], hr, u0[a]) : 0.f;
-        uu = D == 2 ? fmaf(u[0], u[0], u[1] * u[1]) : fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
-        p = fmaf(-float(0.5 * w0), uu, pres_base) * inv_1mw0;
+        for (int a = 0; a < 3; ++a) u[a] = (a < D) ? fma(F[a], hr, u0[a]) : V(0.f);
+        uu = D == 2 ? fma(u[0], u[0], u[1] * u[1]) : fma(u[0], u[0], fma(u[1], u[1], u[2] * u[2]));
+        p = fma(V(-float(0.5 * w0)), uu, pres_base) * inv_1mw0;
 
         // collision: traceless second moments of N - Neq, with sum Neq c c = (c2chi + p) I + u u,
         // in N's storage units (the moments are raw, the u u terms take the scale)
-        const float omega1 = 1.0f - rcp(tau);                                       // 1 - s_nu
-        const float o4 = omega1 * 0.25f;
-        const float pxx = m_xx, pyy = m_yy;
-        // (these products enter the direction sums: __fmul_rn keeps the compiler
-        // from fusing them there in one kernel and not in another)
-        base0 = __fmul_rn(3.0f, u[0]);
-        base1 = __fmul_rn(3.0f, u[1]);
-        base2 = __fmul_rn(3.0f, u[2]);
+        const V omega1 = V(1.0f) - rcp(tau);                                        // 1 - s_nu
+        const V o4 = omega1 * V(0.25f);
+        base0 = V(3.0f) * u[0];
+        base1 = V(3.0f) * u[1];
+        base2 = V(3.0f) * u[2];
         if (D == 2) {
-            A0 = __fmul_rn(o4, fmaf(-sN, fmaf(u[0], u[0], -(u[1] * u[1])), pxx - pyy));     // m7 . f / |m7|^2
-            A1 = 0.f;
-            Axy = __fmul_rn(o4, fmaf(-sN * u[0], u[1], m_xy));                      // m8 . f / |m8|^2
-            Axz = Ayz = 0.f;
+            A0 = o4 * fma(V(-sN), fma(u[0], u[0], -(u[1] * u[1])), m_xx - m_yy);   // m7 . f / |m7|^2
+            A1 = V(0.f);
+            Axy = o4 * fma(V(-sN) * u[0], u[1], m_xy);                              // m8 . f / |m8|^2
+            Axz = Ayz = V(0.f);
         } else {
-            const float pzz = m_zz;
             // 2 ux^2 - uy^2 - uz^2 = 3 ux^2 - u.u
-            A0 = __fmul_rn(omega1 * float(1.0 / 36.0),
-                           fmaf(-sN, fmaf(base0, u[0], -uu), fmaf(2.0f, pxx, -pyy) - pzz));
-            A1 = __fmul_rn(omega1 * float(1.0 / 12.0), fmaf(-sN, fmaf(u[1], u[1], -(u[2] * u[2])), pyy - pzz));
-            const float su0 = -sN * u[0];
-            Axy = __fmul_rn(o4, fmaf(su0, u[1], m_xy));
-            Axz = __fmul_rn(o4, fmaf(su0, u[2], m_xz));
-            Ayz = __fmul_rn(o4, fmaf(-sN * u[1], u[2], m_yz));
+            A0 = (omega1 * V(float(1.0 / 36.0))) * fma(V(-sN), fma(base0, u[0], -uu), fma(V(2.0f), m_xx, -m_yy) - m_zz);
+            A1 = (omega1 * V(float(1.0 / 12.0))) * fma(V(-sN), fma(u[1], u[1], -(u[2] * u[2])), m_yy - m_zz);
+            const V su0 = V(-sN) * u[0];
+            Axy = o4 * fma(su0, u[1], m_xy);
+            Axz = o4 * fma(su0, u[2], m_xz);
+            Ayz = o4 * fma(V(-sN) * u[1], u[2], m_yz);
         }
 
         // segregation: n_phi = grad phi / max(|grad phi|, 1e-6)
-        const float g2 = D == 2 ? fmaf(gp[0], gp[0], gp[1] * gp[1])
-                                : fmaf(gp[0], gp[0], fmaf(gp[1], gp[1], gp[2] * gp[2]));
-        const float inv_gn = inv_norm_floor(g2, 1e-6f);
-        const float kseg = P.two_over_W * phi * (1.0f - phi) * inv_gn;
-        const float ksegB = UNITS ? kseg * sB : kseg;                       // recoloring in B's units
-        phiB = UNITS ? phi * (sB / sN) : phi;                               // phi N*, from N's units to B's
-        const float phmB = UNITS ? (phi - 0.5f) * sB : phi - 0.5f;
-        shb1 = phmB * P.chi[1];
-        shb2 = phmB * P.chi[D == 2 ? 5 : 7];
-        three_p = 3.0f * p;
-        halfF = 1.5f * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
-        const float common = fmaf(-1.5f, uu, three_p);
+        const V g2 = D == 2 ? fma(gp[0], gp[0], gp[1] * gp[1]) : fma(gp[0], gp[0], fma(gp[1], gp[1], gp[2] * gp[2]));
+        const V inv_gn = inv_norm_floor(g2, 1e-6f);
+        const V kseg = V(P.two_over_W) * phi * (V(1.0f) - phi) * inv_gn;
+        const V ksegB = UNITS ? kseg * V(sB) : kseg;                        // recoloring in B's units
+        phiB = UNITS ? phi * V(sB / sN) : phi;                              // phi N*, from N's units to B's
+        const V phmB = UNITS ? (phi - V(0.5f)) * V(sB) : phi - V(0.5f);
+        shb1 = phmB * V(P.chi[1]);
+        shb2 = phmB * V(P.chi[D == 2 ? 5 : 7]);
+        three_p = V(3.0f) * p;
+        halfF = V(1.5f) * inv_rho;   // (1/2) F_i = (3/2) w_i (c_i . F)/rho
+        const V common = fma(V(-1.5f), uu, three_p);
         // per direction class (1 axis, 2 diagonal/edge): the equilibrium's constant
         // part w_i (3p - 3u^2/2) + (chi_i - stored chi_i), divided by w_i, and the
         // recolouring weight ksegB (chi_i + w_i 3p) with the exact chi_i
         constexpr double kW1 = L::w(1), kW2 = L::w(D == 2 ? 5 : 7);
-        common1 = fmaf(P.chi_err[1], float(1.0 / kW1), common);
-        common2 = fmaf(P.chi_err[2], float(1.0 / kW2), common);
-        krc1 = ksegB * fmaf(float(kW1), three_p, P.chi[1] + P.chi_err[1]);
-        krc2 = ksegB * fmaf(float(kW2), three_p, P.chi[D == 2 ? 5 : 7] + P.chi_err[2]);
+        common1 = fma(V(P.chi_err[1]), V(float(1.0 / kW1)), common);
+        common2 = fma(V(P.chi_err[2]), V(float(1.0 / kW2)), common);
+        krc1 = ksegB * fma(V(float(kW1)), three_p, V(P.chi[1] + P.chi_err[1]));
+        krc2 = ksegB * fma(V(float(kW2)), three_p, V(P.chi[D == 2 ? 5 : 7] + P.chi_err[2]));
     }
 
     // Direction i (opp(i) > i) and its opposite o, in storage units: the
     // post-collision N*_i - chi_i, N*_o - chi_o (they share the even part and
     // flip the odd part) and B*_i - chi_i/2, B*_o - chi_o/2 with
     // B* = phi N* + recolor, i.e. phi dN* + (phi - 1/2) chi_i + recolor.
-    __device__ __forceinline__ void dir(const StepParams<float>& P, int i, float& ni, float& no, float& bi,
-                                        float& bo) const {
+    __device__ __forceinline__ void dir(int i, V& ni, V& no, V& bi, V& bo) const {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const float wiN = float(L::w(i)) * sN;
         // the stress projection, 3 c.u, c.F and c.grad phi, each without the terms
         // whose lattice coefficient is zero
-        Acc proj, cu3, cF, cg;
+        Acc<V> proj, cu3, cF, cg;
         if (D == 2) {
             proj.add(cx * cx - cy * cy, A0);
             proj.add(cx * cy, Axy);
@@ -848,35 +910,35 @@ struct FloatNode {
         cu3.add(cy, base1); cF.add(cy, F[1]); cg.add(cy, gp[1]);
         cu3.add(cz, base2); cF.add(cz, F[2]); cg.add(cz, gp[2]);
         const bool axis = cx * cx + cy * cy + cz * cz == 1;
-        const float krc = axis ? krc1 : krc2, g = cg.get();            // recoloring krc (c . grad phi), odd in c
-        const float c3 = cu3.get();
-        const float even = fmaf(wiN, fmaf(0.5f * c3, c3, axis ? common1 : common2), proj.get());
-        const float odd = fmaf(halfF, cF.get(), c3);                   // the odd part over wiN
-        ni = fmaf(wiN, odd, even);
-        no = fmaf(-wiN, odd, even);
-        const float shift_b = axis ? shb1 : shb2;                      // (phi - 1/2) chi_i
-        bi = fmaf(krc, g, fmaf(phiB, ni, shift_b));
-        bo = fmaf(-krc, g, fmaf(phiB, no, shift_b));
+        const V krc = axis ? krc1 : krc2, g = cg.get();                // recoloring krc (c . grad phi), odd in c
+        const V c3 = cu3.get();
+        const V even = fma(V(wiN), fma(V(0.5f) * c3, c3, axis ? common1 : common2), proj.get());
+        const V odd = fma(halfF, cF.get(), c3);                        // the odd part over wiN
+        ni = fma(V(wiN), odd, even);
+        no = fma(V(-wiN), odd, even);
+        const V shift_b = axis ? shb1 : shb2;                          // (phi - 1/2) chi_i
+        bi = fma(krc, g, fma(phiB, ni, shift_b));
+        bo = fma(-krc, g, fma(phiB, no, shift_b));
     }
 
     // Rest direction (no forcing, no stress projection, no recoloring, c_0 = 0),
     // stored exactly (FP32): N*_0 - chi_0 and B*_0 - chi_0/2.
-    __device__ __forceinline__ float rest_N(const StepParams<float>& P) const {
-        return fmaf(-float(1.5 * w0), uu, fmaf(-float(1.0 - w0), three_p, P.chi_err[0]));
+    __device__ __forceinline__ V rest_N(const StepParams<float>& P) const {
+        return fma(V(-float(1.5 * w0)), uu, fma(V(-float(1.0 - w0)), three_p, V(P.chi_err[0])));
     }
-    __device__ __forceinline__ float rest_B(const StepParams<float>& P, float nst0) const {
-        return fmaf(phi, nst0, (phi - 0.5f) * P.chi[0]);
+    __device__ __forceinline__ V rest_B(const StepParams<float>& P, V nst0) const {
+        return fma(phi, nst0, (phi - V(0.5f)) * V(P.chi[0]));
     }
     // With FP16 storage the float rest populations take the node totals the
     // collision fixes less the moving populations as stored (sumN, sumB in
-    // storage units): sum_i (N*_i - chi_i) = 0 for any N, u, p and F (the
-    // equilibrium sums to sum chi = 1; the stress projection and the forcing
-    // have no zeroth moment) and sum_i (B*_i - chi_i/2) = phi - 1/2 (the
+    // storage units, one node each): sum_i (N*_i - chi_i) = 0 for any N, u, p
+    // and F (the equilibrium sums to sum chi = 1; the stress projection and the
+    // forcing have no zeroth moment) and sum_i (B*_i - chi_i/2) = phi - 1/2 (the
     // recoloring is odd in c), so FP16 rounding moves no mass between the
     // phases or out of the domain.
     __device__ __forceinline__ static float rest_N_from_sum(float sumN) { return -sumN * (1.0f / kScaleN); }
-    __device__ __forceinline__ float rest_B_from_sum(float sumB) const {
-        return fmaf(-sumB, 1.0f / kScaleB, phi - 0.5f);
+    __device__ __forceinline__ static float rest_B_from_sum(float sumB, float phi_node) {
+        return fmaf(-sumB, 1.0f / kScaleB, phi_node - 0.5f);
     }
 };
 
@@ -971,26 +1033,38 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     } else {
     static_assert(kPairs && kShift, "float arithmetic runs on deviations, summed over +/- pairs");
     constexpr bool kUnits = !PS::kExact;
-    FloatNode<Q, kUnits, CONTRAST> nd;
-    nd.compute(P, N, phi, gp, lsum, du);
+    using FN = FloatNode<Q, kUnits, CONTRAST, SF>;
+    FN nd;
+    {
+        SF Ns[Q], gps[3], gus[3][3];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Ns[i] = SF(N[i]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gps[a] = SF(gp[a]);
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) gus[a][bb] = SF(du[a][bb]);
+        }
+        nd.compute(P, Ns, SF(phi), gps, SF(lsum), gus);
+    }
 
     // u and p: FP16 storage writes them before the populations, which frees
     // their registers for the stored sums (no spills in the batched kernels);
     // FP32 writes them last, measured 0.7% faster
     auto store_u_p = [&]() {
 #pragma unroll
-        for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = nd.u[a];
-        b.p[node] = nd.p;
-        if (!(nd.uu < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
+        for (int a = 0; a < D; ++a) b.u_out[a * pl + node] = nd.u[a].v;
+        b.p[node] = nd.p.v;
+        if (!(nd.uu.v < T(1e30))) atomicOr(b.err, kErrNonFinite);   // also catches NaN
     };
     if constexpr (!PS::kExact) store_u_p();
 
     auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
     auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
     if constexpr (PS::kExact) {
-        const T nst0 = nd.rest_N(P);
-        PS::store_rest(PS::rest(b.Nout), node, nst0);
-        PS::store_rest(PS::rest(b.Bout), node, nd.rest_B(P, nst0));
+        const SF nst0 = nd.rest_N(P);
+        PS::store_rest(PS::rest(b.Nout), node, nst0.v);
+        PS::store_rest(PS::rest(b.Bout), node, nd.rest_B(P, nst0).v);
     }
     // sums of the moving populations as stored (FP16 storage)
     T sumN = T(0), sumB = T(0);
@@ -998,16 +1072,16 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
-        T ni, no, bi, bo;
-        nd.dir(P, i, ni, no, bi, bo);
-        PS::store_units(Nmov, (i - 1) * pl + node, ni, sumN);
-        PS::store_units(Nmov, (o - 1) * pl + node, no, sumN);
-        PS::store_units(Bmov, (i - 1) * pl + node, bi, sumB);
-        PS::store_units(Bmov, (o - 1) * pl + node, bo, sumB);
+        SF ni, no, bi, bo;
+        nd.dir(i, ni, no, bi, bo);
+        PS::store_units(Nmov, (i - 1) * pl + node, ni.v, sumN);
+        PS::store_units(Nmov, (o - 1) * pl + node, no.v, sumN);
+        PS::store_units(Bmov, (i - 1) * pl + node, bi.v, sumB);
+        PS::store_units(Bmov, (o - 1) * pl + node, bo.v, sumB);
     }
     if constexpr (!PS::kExact) {
-        PS::store_rest(PS::rest(b.Nout), node, FloatNode<Q, kUnits, CONTRAST>::rest_N_from_sum(sumN));
-        PS::store_rest(PS::rest(b.Bout), node, nd.rest_B_from_sum(sumB));
+        PS::store_rest(PS::rest(b.Nout), node, FN::rest_N_from_sum(sumN));
+        PS::store_rest(PS::rest(b.Bout), node, FN::rest_B_from_sum(sumB, nd.phi.v));
     }
     if constexpr (PS::kExact) store_u_p();
     }

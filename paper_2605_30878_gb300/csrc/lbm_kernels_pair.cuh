@@ -12,7 +12,10 @@
 //     directions of that row),
 //   - its stores of N*, B*, u and p (one two-wide store each),
 // which halves the load/store and address instructions per node of the
-// one-node kernel.  Blocks are 32 x TY x TZ threads covering 64 x TY x TZ
+// one-node kernel.  The float arithmetic of the two nodes runs on packed
+// pairs (FloatNode<..., F2>: one add/mul/fma.f32x2 for both nodes, each lane
+// rounded as the one-node kernel's scalar operation), which halves the float
+// instructions too.  Blocks are 32 x TY x TZ threads covering 64 x TY x TZ
 // nodes; the halo tile is copied by the same halo_issue/halo_complete as
 // k_step's (TMA boxes 72 x (TY + 2) x (TZ + 2) on interior tiles).  A node of
 // the pair that is not fluid gets zero velocity and pressure; its population
@@ -41,13 +44,11 @@ struct PairTile {
 };
 
 // Resident blocks per SM the pair kernel is compiled for (registers per
-// thread <= 65536 / (THREADS * blocks)), measured at 192^3: FP32 storage runs
-// best at 6 (80 registers; 7 blocks at 72 registers spill 20 bytes and run 4%
-// slower), FP16 storage at 7 (3% faster than 6: its bytes per node are fewer,
-// so more warps in flight pay for the spill); 4 is 20% slower, 8 spills 76
-// bytes or more.
+// thread <= 65536 / (THREADS * blocks)), measured at 192^3 with the packed
+// node update: 6 (80 registers, no spills) for FP32 and FP16 storage; 7 (72
+// registers) spills 50 bytes with FP16 storage and runs 9% slower; 4 is 20%
+// slower; 8 spills 76 bytes or more.
 template <typename S> struct PairBlocks { static constexpr int value = 6; };
-template <> struct PairBlocks<__half> { static constexpr int value = 7; };
 
 // The values at halo slots hc + o and hc + o + 1 (hc even): one aligned
 // two-wide load for even o, else the odd half of the pair below and the even
@@ -127,58 +128,61 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
                     NB[i] = (float)PS::load_units(mv, idx_checked((L::opp(i) - 1) * pl + nodeA + 1, nmv, err));
         }
     }
-    // the moments of both nodes while the halo copy completes; the pulled
-    // values are then dead, which keeps them out of the registers the stencils need
-    FloatNode<Q, kUnits, CONTRAST> nA, nB;
-    nA.moments(NA);
-    nB.moments(NB);
+    // the moments of both nodes (one packed lane each) while the halo copy
+    // completes; the pulled values are then dead, which keeps them out of the
+    // registers the stencils need
+    FloatNode<Q, kUnits, CONTRAST, F2> n2;
+    {
+        F2 N2[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) N2[i] = F2(NA[i], NB[i]);
+        n2.moments(N2);
+    }
     const bool halo_ok = halo_complete<Tl, float, S>(b, interior, bar, s_phi, s_u, fix_v, fix_at);
     __syncthreads();
     if (!(fluidA || fluidB) || !halo_ok) return;
 
     // isotropic stencils of both nodes, over +/- pairs in the order of k_step
     const int hcA = (2 * threadIdx.x + Tl::XO) + Tl::HX * ((threadIdx.y + 1) + Tl::HY * (D == 2 ? 0 : threadIdx.z + 1));
-    const float2 ph = halo_pair<Tl::HN>(s_phi, hcA, 0, err);
-    float gA[3] = {0.f, 0.f, 0.f}, gB[3] = {0.f, 0.f, 0.f};
-    float lA = 0.f, lB = 0.f;
-    float dA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float dB[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    const float2 phv = halo_pair<Tl::HN>(s_phi, hcA, 0, err);
+    const F2 ph(phv.x, phv.y);
+    F2 g[3] = {F2(0.f), F2(0.f), F2(0.f)}, lap(0.f);
+    F2 du[3][3] = {{F2(0.f), F2(0.f), F2(0.f)}, {F2(0.f), F2(0.f), F2(0.f)}, {F2(0.f), F2(0.f), F2(0.f)}};
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const float wi = float(3.0 * L::w(i)), wl = float(6.0 * L::w(i));   // grad: 3 w_i, lap: 6 w_i
         const int o = Tl::off(cx, cy, cz);
-        const float2 pp = halo_pair<Tl::HN>(s_phi, hcA, o, err), pm = halo_pair<Tl::HN>(s_phi, hcA, -o, err);
-        const float dphiA = pp.x - pm.x, dphiB = pp.y - pm.y;
-        if (cx) { gA[0] = fmaf(float(cx) * wi, dphiA, gA[0]); gB[0] = fmaf(float(cx) * wi, dphiB, gB[0]); }
-        if (cy) { gA[1] = fmaf(float(cy) * wi, dphiA, gA[1]); gB[1] = fmaf(float(cy) * wi, dphiB, gB[1]); }
-        if (cz) { gA[2] = fmaf(float(cz) * wi, dphiA, gA[2]); gB[2] = fmaf(float(cz) * wi, dphiB, gB[2]); }
-        lA = fmaf(wl, (pp.x - ph.x) + (pm.x - ph.x), lA);
-        lB = fmaf(wl, (pp.y - ph.y) + (pm.y - ph.y), lB);
+        const float2 ppv = halo_pair<Tl::HN>(s_phi, hcA, o, err), pmv = halo_pair<Tl::HN>(s_phi, hcA, -o, err);
+        const F2 pp(ppv.x, ppv.y), pm(pmv.x, pmv.y);
+        const F2 dphi = pp - pm;
+        if (cx) g[0] = fma(F2(float(cx) * wi), dphi, g[0]);
+        if (cy) g[1] = fma(F2(float(cy) * wi), dphi, g[1]);
+        if (cz) g[2] = fma(F2(float(cz) * wi), dphi, g[2]);
+        lap = fma(F2(wl), (pp - ph) + (pm - ph), lap);
         if (CONTRAST) {
 #pragma unroll
             for (int bb = 0; bb < D; ++bb) {
-                const float2 up = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, o, err);
-                const float2 um = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, -o, err);
-                const float duA = up.x - um.x, duB = up.y - um.y;
-                if (cx) { dA[0][bb] = fmaf(float(cx) * wi, duA, dA[0][bb]); dB[0][bb] = fmaf(float(cx) * wi, duB, dB[0][bb]); }
-                if (cy) { dA[1][bb] = fmaf(float(cy) * wi, duA, dA[1][bb]); dB[1][bb] = fmaf(float(cy) * wi, duB, dB[1][bb]); }
-                if (cz) { dA[2][bb] = fmaf(float(cz) * wi, duA, dA[2][bb]); dB[2][bb] = fmaf(float(cz) * wi, duB, dB[2][bb]); }
+                const float2 upv = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, o, err);
+                const float2 umv = halo_pair<D * Tl::HN>(s_u, hcA + bb * Tl::HN, -o, err);
+                const F2 dub = F2(upv.x, upv.y) - F2(umv.x, umv.y);
+                if (cx) du[0][bb] = fma(F2(float(cx) * wi), dub, du[0][bb]);
+                if (cy) du[1][bb] = fma(F2(float(cy) * wi), dub, du[1][bb]);
+                if (cz) du[2][bb] = fma(F2(float(cz) * wi), dub, du[2][bb]);
             }
         }
     }
-    nA.compute(P, ph.x, gA, lA, dA);
-    nB.compute(P, ph.y, gB, lB, dB);
+    n2.compute(P, ph, g, lap, du);
 
     // u and p of the pair in one store per field; 0 at a node that is not fluid
     // (the velocity halo reads 0 at solid nodes)
 #pragma unroll
     for (int a = 0; a < D; ++a)
         *reinterpret_cast<float2*>(b.u_out + a * pl + nodeA) =
-            make_float2(fluidA ? nA.u[a] : 0.f, fluidB ? nB.u[a] : 0.f);
-    *reinterpret_cast<float2*>(b.p + nodeA) = make_float2(fluidA ? nA.p : 0.f, fluidB ? nB.p : 0.f);
-    if ((fluidA && !(nA.uu < 1e30f)) || (fluidB && !(nB.uu < 1e30f))) atomicOr(err, kErrNonFinite);
+            make_float2(fluidA ? n2.u[a].lo() : 0.f, fluidB ? n2.u[a].hi() : 0.f);
+    *reinterpret_cast<float2*>(b.p + nodeA) = make_float2(fluidA ? n2.p.lo() : 0.f, fluidB ? n2.p.hi() : 0.f);
+    if ((fluidA && !(n2.uu.lo() < 1e30f)) || (fluidB && !(n2.uu.hi() < 1e30f))) atomicOr(err, kErrNonFinite);
 
     auto* __restrict__ Nmov = PS::moving(b.Nout, pl);
     auto* __restrict__ Bmov = PS::moving(b.Bout, pl);
@@ -187,23 +191,22 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
-        float niA, noA, biA, boA, niB, noB, biB, boB;
-        nA.dir(P, i, niA, noA, biA, boA);
-        nB.dir(P, i, niB, noB, biB, boB);
-        PS::store_units2(Nmov, (i - 1) * pl + nodeA, niA, niB, sNA, sNB);
-        PS::store_units2(Nmov, (o - 1) * pl + nodeA, noA, noB, sNA, sNB);
-        PS::store_units2(Bmov, (i - 1) * pl + nodeA, biA, biB, sBA, sBB);
-        PS::store_units2(Bmov, (o - 1) * pl + nodeA, boA, boB, sBA, sBB);
+        F2 ni, no, bi, bo;
+        n2.dir(i, ni, no, bi, bo);
+        PS::store_units2(Nmov, (i - 1) * pl + nodeA, ni.lo(), ni.hi(), sNA, sNB);
+        PS::store_units2(Nmov, (o - 1) * pl + nodeA, no.lo(), no.hi(), sNA, sNB);
+        PS::store_units2(Bmov, (i - 1) * pl + nodeA, bi.lo(), bi.hi(), sBA, sBB);
+        PS::store_units2(Bmov, (o - 1) * pl + nodeA, bo.lo(), bo.hi(), sBA, sBB);
     }
     float2 rn, rb;
     if constexpr (PS::kExact) {
-        const float n0A = nA.rest_N(P), n0B = nB.rest_N(P);
-        rn = make_float2(n0A, n0B);
-        rb = make_float2(nA.rest_B(P, n0A), nB.rest_B(P, n0B));
+        const F2 n0 = n2.rest_N(P), b0 = n2.rest_B(P, n0);
+        rn = make_float2(n0.lo(), n0.hi());
+        rb = make_float2(b0.lo(), b0.hi());
     } else {
-        using FN = FloatNode<Q, kUnits, CONTRAST>;
+        using FN = FloatNode<Q, kUnits, CONTRAST, F2>;
         rn = make_float2(FN::rest_N_from_sum(sNA), FN::rest_N_from_sum(sNB));
-        rb = make_float2(nA.rest_B_from_sum(sBA), nB.rest_B_from_sum(sBB));
+        rb = make_float2(FN::rest_B_from_sum(sBA, n2.phi.lo()), FN::rest_B_from_sum(sBB, n2.phi.hi()));
     }
     *reinterpret_cast<float2*>(PS::rest(b.Nout) + nodeA) = rn;
     *reinterpret_cast<float2*>(PS::rest(b.Bout) + nodeA) = rb;
