@@ -1262,6 +1262,12 @@ struct lbm_batch {
     std::vector<int> cur0;             // each domain's buffer parity when the batch was made
     int parity = 0;                    // steps taken by the batch, mod 2
     int variant = 0;
+    // tile shape of the color kernel: 3 (32 x 2 x 2 in 3D, 32 x 2 in 2D),
+    // whatever shape the step kernels use.  The color kernel has no halo, and
+    // narrower tiles leave fewer lanes idle at the ragged x ends of small
+    // domains (config 4: 3.305 ms per step against 3.331 on the step's 64-wide
+    // tiles).  LBM_BATCH_PHI_SHAPE=step: the step's shape; =0..5: that shape.
+    int phi_shape = 3;
     int ntiles[kTileVariants] = {};
     int ncontrast[kTileVariants] = {};           // tiles of domains with density contrast come first
     int device = 0;
@@ -1334,8 +1340,9 @@ void batch_launch_step(lbm_batch* b, int parity, cudaStream_t s) {
     bdispatch(b->precision, [&](auto Lx) {
         using L = decltype(Lx);
         L::ghost_batched(b->GK, b->ghost_tabs, b->ghost_begin, (int)b->doms.size(), b->total_ghosts, s);
+        const int Vp = b->phi_shape < 0 ? V : b->phi_shape;
         L::step_phi_batched(b->Q, V, b->tiles[V], b->maps + (size_t)V * kBatchSlots * 3, b->ntiles[V],
-                            b->ncontrast[V], parity, s);
+                            b->ncontrast[V], Vp, b->tiles[Vp], b->ntiles[Vp], parity, s);
     });
 }
 
@@ -1392,6 +1399,10 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
         b->cur0.push_back(doms[i]->cur);
     }
     b->stream = (cudaStream_t)cuda_stream;
+    const char* phi_shape = std::getenv("LBM_BATCH_PHI_SHAPE");
+    if (phi_shape && std::strcmp(phi_shape, "step") == 0) b->phi_shape = -1;
+    else if (phi_shape && phi_shape[0] >= '0' && phi_shape[0] < '0' + kTileVariants && !phi_shape[1])
+        b->phi_shape = phi_shape[0] - '0';
     if (n > kBatchSlots) {
         delete b;
         return bfail(nullptr, LBM_ERR_ARG, "a batch holds at most " + std::to_string(kBatchSlots) + " domains");

@@ -86,7 +86,7 @@ struct Launch {
     // step kernels then color kernel of every domain (the ghost update precedes them);
     // tiles[0, ncontrast) belong to domains with density contrast
     static void step_phi_batched(int Q, int V, const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast,
-                                 int parity, cudaStream_t s);
+                                 int Vphi, const int4* phi_tiles, int phi_ntiles, int parity, cudaStream_t s);
     // Slot tables: entry_size() bytes per domain, filled by fill_entry, copied
     // to slots [slot0, slot0 + n) of the constant table by upload_entries.
     static size_t entry_size() { return sizeof(BatchEntry<T, S>); }

@@ -3,6 +3,8 @@
 // Launch<T, S> (and so every kernel) once each.
 #pragma once
 
+#include <type_traits>
+
 #include <cmath>
 
 #include "lbm_launch.cuh"
@@ -238,31 +240,38 @@ void Launch<T, S>::step_batched_v(const int4* tiles, const CUtensorMap* maps, in
             k_step_batched<Qc, T, S, V, false><<<ntiles - ncontrast, block, 0, s>>>(tiles + ncontrast, maps,
                                                                                     parity);
     }
-    k_phi_batched<Qc, T, S, V><<<ntiles, block, 0, s>>>(tiles, parity);
 }
 
 // step kernels then color kernel of every domain (the ghost update precedes them);
 // tiles[0, ncontrast) belong to domains with density contrast
 template <typename T, typename S>
 void Launch<T, S>::step_phi_batched(int Q, int V, const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast,
-                                      int parity,
-                             cudaStream_t s) {
+                                    int Vphi, const int4* phi_tiles, int phi_ntiles, int parity, cudaStream_t s) {
     if (ntiles == 0) return;
-    if (Q == 9) {
-        if (V == 0) step_batched_v<9, 0>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 1) step_batched_v<9, 1>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 2) step_batched_v<9, 2>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 3) step_batched_v<9, 3>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 4) step_batched_v<9, 4>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 5) step_batched_v<9, 5>(tiles, maps, ntiles, ncontrast, parity, s);
-    } else {
-        if (V == 0) step_batched_v<19, 0>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 1) step_batched_v<19, 1>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 2) step_batched_v<19, 2>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 3) step_batched_v<19, 3>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 4) step_batched_v<19, 4>(tiles, maps, ntiles, ncontrast, parity, s);
-        if (V == 5) step_batched_v<19, 5>(tiles, maps, ntiles, ncontrast, parity, s);
-    }
+    auto steps = [&](auto q) {
+        constexpr int Qc = decltype(q)::value;
+        if (V == 0) step_batched_v<Qc, 0>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 1) step_batched_v<Qc, 1>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 2) step_batched_v<Qc, 2>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 3) step_batched_v<Qc, 3>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 4) step_batched_v<Qc, 4>(tiles, maps, ntiles, ncontrast, parity, s);
+        if (V == 5) step_batched_v<Qc, 5>(tiles, maps, ntiles, ncontrast, parity, s);
+        // the color kernel on its own tile list (it needs no halo, so its shape
+        // need not be the step's)
+        auto phi = [&](auto v) {
+            constexpr int Vc = decltype(v)::value;
+            using Tl = Tile<Qc, Vc>;
+            k_phi_batched<Qc, T, S, Vc><<<phi_ntiles, dim3(Tl::TX, Tl::TY, Tl::TZ), 0, s>>>(phi_tiles, parity);
+        };
+        if (Vphi == 0) phi(std::integral_constant<int, 0>{});
+        if (Vphi == 1) phi(std::integral_constant<int, 1>{});
+        if (Vphi == 2) phi(std::integral_constant<int, 2>{});
+        if (Vphi == 3) phi(std::integral_constant<int, 3>{});
+        if (Vphi == 4) phi(std::integral_constant<int, 4>{});
+        if (Vphi == 5) phi(std::integral_constant<int, 5>{});
+    };
+    if (Q == 9) steps(std::integral_constant<int, 9>{});
+    else steps(std::integral_constant<int, 19>{});
 }
 
 template <typename T, typename S>
