@@ -1087,24 +1087,42 @@ __device__ __forceinline__ void step_node(const StepParams<T>& P, const StepBuff
     }
 }
 
+// The periodic images of x = -1 and x = nx that a block at an x end of the
+// grid patches into its halo after a tiled copy: one per halo row and field
+// at each end, K per thread (1 unless the block has fewer threads than both
+// ends' images).
+template <class Tl, typename T, bool CONTRAST>
+struct HaloFix {
+    static constexpr int kFields = CONTRAST ? 1 + Tl::D : 1;
+    static constexpr int kRows = Tl::HY * Tl::HZ;
+    static constexpr int kPerCol = kRows * kFields;
+    static constexpr int K = (2 * kPerCol + Tl::THREADS - 1) / Tl::THREADS;
+    T v[K];
+    int at[K];                                 // halo slot (phi, then the u fields), or -1
+};
+
 // A block's halo tile (color, and the previous velocity with a density
 // contrast) with a one-node ring: issued by halo_issue, waited for by
 // halo_complete, shared by the step kernels of every tile shape.  With maps
 // (tiles whose halo needs no periodic image in y and z) two tiled TMA copies
 // fill it, completed on the mbarrier `bar`; at the x ends of the grid the box
 // reads zeros where x < 0 or x >= nx, and the stencil needs the periodic
-// images of x = -1 and x = nx there: one thread per halo row and field loads
-// such a value now and writes it once the copy has landed (fix_at >= 0).
-// Without maps the halo is copied element by element with cp.async.
-// halo_issue returns false when the debug bounds checks reject the tile's box.
+// images of x = -1 and x = nx there: the threads load those values now (fx)
+// and write them once the copy has landed.  Without maps the halo is copied
+// element by element with cp.async.  halo_issue returns false when the debug
+// bounds checks reject the tile's box.
 template <class Tl, typename T, typename S, bool CONTRAST>
 __device__ __forceinline__ bool halo_issue(const StepParams<T>& P, const StepBuffers<T, S>& b, T* s_phi, T* s_u,
                                            int x0, int y0, int z0, const CUtensorMap* tm_phi,
-                                           const CUtensorMap* tm_u, uint64_t* bar, T& fix_v, int& fix_at) {
+                                           const CUtensorMap* tm_u, uint64_t* bar, HaloFix<Tl, T, CONTRAST>& fx) {
+    using Fx = HaloFix<Tl, T, CONTRAST>;
     const bool tma = tm_phi != nullptr;
-    fix_v = T(0);
-    fix_at = -1;
-    constexpr int kHaloFields = CONTRAST ? 1 + Tl::D : 1;
+#pragma unroll
+    for (int j = 0; j < Fx::K; ++j) {
+        fx.v[j] = T(0);
+        fx.at[j] = -1;
+    }
+    constexpr int kHaloFields = Fx::kFields;
     if (tma && kDebugBounds) {
         // the box of a tiled copy: x origin on a 16-byte boundary, the whole
         // halo inside the grid in y and z (no periodic image needed there)
@@ -1125,19 +1143,23 @@ __device__ __forceinline__ bool halo_issue(const StepParams<T>& P, const StepBuf
             if (CONTRAST) tma_load_4d(s_u, tm_u, x0 - Tl::XO, y0 - 1, zc, 0, bar);
         }
         const bool lo = x0 == 0, hi = x0 + Tl::TX >= P.nx;
-        constexpr int kRows = Tl::HY * Tl::HZ, kPerCol = kRows * kHaloFields;
-        // one thread per periodic image to patch: both x ends of a one-tile-wide grid at once
-        static_assert(Tl::THREADS >= 2 * kPerCol, "too few threads to patch the x-end halo columns");
-        if ((lo || hi) && tid < (int(lo) + int(hi)) * kPerCol) {
-            const bool left = lo && tid < kPerCol;              // x = -1, else x = nx
-            const int k = tid % kPerCol, field = k / kRows, r = k % kRows;
+        constexpr int kRows = Fx::kRows, kPerCol = Fx::kPerCol;
+        // image t of both x ends of a one-tile-wide grid at once: thread tid
+        // takes t = tid, tid + THREADS, ...
+        const int count = (int(lo) + int(hi)) * kPerCol;
+#pragma unroll
+        for (int j = 0; j < Fx::K; ++j) {
+            const int t = tid + j * Tl::THREADS;
+            if (t >= count) continue;
+            const bool left = lo && t < kPerCol;                // x = -1, else x = nx
+            const int k = t % kPerCol, field = k / kRows, r = k % kRows;
             const int hy = r % Tl::HY, hz = r / Tl::HY;
             const int gz = Tl::D == 2 ? 0 : z0 - 1 + hz;
             const int node = (left ? P.nx - 1 : 0) + P.px * (y0 - 1 + hy + P.ny * gz);
             const int fn = idx_checked(node, P.plane, b.err);
-            fix_v = field == 0 ? b.phi[fn] : b.u_in[(field - 1) * (int)P.plane + fn];
-            fix_at = (field == 0 ? 0 : Tl::HN * field) + (left ? Tl::XO - 1 : P.nx - x0 + Tl::XO) + Tl::HX * r;
-            if (!idx_ok(fix_at, kHaloFields * Tl::HN, b.err)) fix_at = -1;
+            fx.v[j] = field == 0 ? b.phi[fn] : b.u_in[(field - 1) * (int)P.plane + fn];
+            fx.at[j] = (field == 0 ? 0 : Tl::HN * field) + (left ? Tl::XO - 1 : P.nx - x0 + Tl::XO) + Tl::HX * r;
+            if (!idx_ok(fx.at[j], kHaloFields * Tl::HN, b.err)) fx.at[j] = -1;
         }
     } else {
         load_halo<Tl, T, CONTRAST>(P, b.phi, b.u_in, s_phi, s_u, x0, y0, z0, b.err);
@@ -1148,9 +1170,9 @@ __device__ __forceinline__ bool halo_issue(const StepParams<T>& P, const StepBuf
 // Waits for the halo issued by halo_issue and patches the x-end images;
 // false if a tiled copy did not complete within the bounded wait.  The
 // caller's barrier follows.
-template <class Tl, typename T, typename S>
+template <class Tl, typename T, typename S, class Fx>
 __device__ __forceinline__ bool halo_complete(const StepBuffers<T, S>& b, bool tma, uint64_t* bar, T* s_phi,
-                                              T* s_u, T fix_v, int fix_at) {
+                                              T* s_u, const Fx& fx) {
     if (!tma) {
         cp_async_wait_all();
         return true;
@@ -1164,7 +1186,9 @@ __device__ __forceinline__ bool halo_complete(const StepBuffers<T, S>& b, bool t
         if (threadIdx.x + threadIdx.y + threadIdx.z == 0) atomicOr(b.err, kErrCopyTimeout);
         mbar_wait(bar, 0);
     }
-    if (halo_ok && fix_at >= 0) (fix_at < Tl::HN ? s_phi : s_u - Tl::HN)[fix_at] = fix_v;
+#pragma unroll
+    for (int j = 0; j < Fx::K; ++j)
+        if (halo_ok && fx.at[j] >= 0) (fx.at[j] < Tl::HN ? s_phi : s_u - Tl::HN)[fx.at[j]] = fx.v[j];
     return halo_ok;
 }
 
@@ -1177,9 +1201,8 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
                                           const CUtensorMap* tm_u = nullptr, uint64_t* bar = nullptr) {
     using Tl = Tile<Q, V>;
     const bool tma = tm_phi != nullptr;
-    T fix_v;
-    int fix_at;
-    if (!halo_issue<Tl, T, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, tm_phi, tm_u, bar, fix_v, fix_at)) return;
+    HaloFix<Tl, T, CONTRAST> fx;
+    if (!halo_issue<Tl, T, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, tm_phi, tm_u, bar, fx)) return;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     const bool in_grid = x < P.nx && y < P.ny && z < P.nz;
     const int node = in_grid ? idx_checked(x + P.px * (y + P.ny * z), P.plane, b.err) : 0;
@@ -1188,7 +1211,7 @@ __device__ __forceinline__ void step_tile(const StepParams<T>& P, const StepBuff
     if (in_grid) pull_streaming<Q, T, S>(P, b.Nin, node, x, y, z, N, b.err);      // in flight with the mask load
     const bool fluid = !(m & MASK_NOT_FLUID);
     if (fluid && (m & ~MASK_NOT_FLUID)) pull_bounce_back<Q, T, S>(P, b.Nin, m, node, N, b.err);
-    const bool halo_ok = halo_complete<Tl, T, S>(b, tma, bar, s_phi, s_u, fix_v, fix_at);
+    const bool halo_ok = halo_complete<Tl, T, S>(b, tma, bar, s_phi, s_u, fx);
     __syncthreads();
     if (fluid && halo_ok) step_node<Q, V, T, S, CONTRAST>(P, b, s_phi, s_u, N, node);
 }

@@ -27,11 +27,13 @@
 
 namespace lbmgpu {
 
-template <int Q>
+// TXn nodes along x (64: the single-domain kernel and batch shape 5; 32:
+// batch shape 3, narrower tiles for small domains' ragged x ends)
+template <int Q, int TXn = 64>
 struct PairTile {
     static constexpr int D = Lattice<Q>::D;
-    static constexpr int BX = 32;                  // threads along x
-    static constexpr int TX = 2 * BX;              // nodes along x
+    static constexpr int BX = TXn / 2;             // threads along x
+    static constexpr int TX = TXn;                 // nodes along x
     static constexpr int TY = D == 2 ? 4 : 2;
     static constexpr int TZ = D == 2 ? 1 : 2;
     static constexpr int XO = 4;                   // halo origin x0 - 4: 16-byte aligned for tiled copies
@@ -48,7 +50,7 @@ struct PairTile {
 // node update: 6 (80 registers, no spills) for FP32 and FP16 storage; 7 (72
 // registers) spills 50 bytes with FP16 storage and runs 9% slower; 4 is 20%
 // slower; 8 spills 76 bytes or more.
-template <typename S> struct PairBlocks { static constexpr int value = 6; };
+template <typename S, int THREADS = 128> struct PairBlocks { static constexpr int value = 6 * 128 / THREADS; };
 
 // The values at halo slots hc + o and hc + o + 1 (hc even): one aligned
 // two-wide load for even o, else the odd half of the pair below and the even
@@ -65,22 +67,20 @@ __device__ __forceinline__ float2 halo_pair(const float* s, int hc, int o, int* 
 // The pair tile at (x0, y0, z0); maps != nullptr: tiled halo copies (the
 // caller checked the tile needs no periodic image in y and z and initialised
 // the barrier).
-template <int Q, typename S, bool CONTRAST>
+template <int Q, typename S, bool CONTRAST, int TXn = 64>
 __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const StepBuffers<float, S>& b,
                                                float* s_phi, float* s_u, int x0, int y0, int z0,
                                                const CUtensorMap* tm_phi, const CUtensorMap* tm_u,
                                                uint64_t* bar) {
-    using Tl = PairTile<Q>;
+    using Tl = PairTile<Q, TXn>;
     using L = Lattice<Q>;
     using PS = PopStore<S>;
     constexpr int D = L::D;
     constexpr bool kUnits = !PS::kExact;
     int* const err = b.err;
     const bool interior = tm_phi != nullptr;
-    float fix_v;
-    int fix_at;
-    if (!halo_issue<Tl, float, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, tm_phi, tm_u, bar, fix_v, fix_at))
-        return;
+    HaloFix<Tl, float, CONTRAST> fx;
+    if (!halo_issue<Tl, float, S, CONTRAST>(P, b, s_phi, s_u, x0, y0, z0, tm_phi, tm_u, bar, fx)) return;
 
     // the pair's populations, pulled while the halo is in flight
     const int xa = x0 + 2 * threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
@@ -138,7 +138,7 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
         for (int i = 0; i < Q; ++i) N2[i] = F2(NA[i], NB[i]);
         n2.moments(N2);
     }
-    const bool halo_ok = halo_complete<Tl, float, S>(b, interior, bar, s_phi, s_u, fix_v, fix_at);
+    const bool halo_ok = halo_complete<Tl, float, S>(b, interior, bar, s_phi, s_u, fx);
     __syncthreads();
     if (!(fluidA || fluidB) || !halo_ok) return;
 
@@ -238,11 +238,12 @@ __global__ void __launch_bounds__(PairTile<Q>::THREADS, PairBlocks<S>::value)
 }
 
 // Batched form: one pair tile of one domain per block, the domain's
-// parameters in its constant-memory slot (as k_step_batched, tile shape 5).
-template <int Q, typename S, bool CONTRAST>
-__global__ void __launch_bounds__(PairTile<Q>::THREADS, PairBlocks<S>::value)
+// parameters in its constant-memory slot (as k_step_batched): 64 nodes wide
+// for tile shape 5, 32 for tile shape 3.
+template <int Q, typename S, bool CONTRAST, int TXn = 64>
+__global__ void __launch_bounds__(PairTile<Q, TXn>::THREADS, (PairBlocks<S, PairTile<Q, TXn>::THREADS>::value))
     k_step_pair_batched(const int4* __restrict__ tiles, const CUtensorMap* __restrict__ maps, int parity) {
-    using Tl = PairTile<Q>;
+    using Tl = PairTile<Q, TXn>;
     constexpr int D = Tl::D;
     __shared__ __align__(128) float s_phi[Tl::HN];
     __shared__ __align__(128) float s_u[CONTRAST ? D * Tl::HN : 2];
@@ -259,8 +260,8 @@ __global__ void __launch_bounds__(PairTile<Q>::THREADS, PairBlocks<S>::value)
         if (threadIdx.x + threadIdx.y + threadIdx.z == 0) mbar_init(&s_bar, 1);
         __syncthreads();                                      // the barrier exists before anyone waits on it
     }
-    step_pair_tile<Q, S, CONTRAST>(e.P, e.b[parity], s_phi, s_u, t.y, y0, z0, tma ? maps + 3 * t.x : nullptr,
-                                   maps + 3 * t.x + 1 + parity, &s_bar);
+    step_pair_tile<Q, S, CONTRAST, TXn>(e.P, e.b[parity], s_phi, s_u, t.y, y0, z0, tma ? maps + 3 * t.x : nullptr,
+                                        maps + 3 * t.x + 1 + parity, &s_bar);
 }
 
 }  // namespace lbmgpu
