@@ -321,11 +321,13 @@ lbm_status lbm_batch_sync(lbm_batch* b);
 
 /* Block tile shapes of the batched step kernels, in nodes (shape 0 is the
  * tile of the single-domain one-node kernel, shape 5 that of the two-node
- * kernel, whose threads update two x-adjacent nodes each in float arithmetic):
- *            0        1        2        3        4        5
- *   D3Q19  32x4x2   32x2x4   32x8x1   32x2x2   32x4x4   64x2x2
- *   D2Q9   32x8     64x4     128x2    32x4     32x16    64x4
- *   threads 256      256      256      128      512      128 (FP64: 256) */
+ * kernel, whose threads update two x-adjacent nodes each; float arithmetic
+ * runs shapes 0, 3 and 5 with two nodes per thread):
+ *                    0        1        2        3        4        5
+ *   D3Q19          32x4x2   32x2x4   32x8x1   32x2x2   32x4x4   64x2x2
+ *   D2Q9           32x8     64x4     128x2    32x4     32x16    64x4
+ *   threads float   128      256      256      64       512      128
+ *   threads FP64    256      256      256      128      512      256 */
 enum { LBM_BATCH_TILE_SHAPES = 6 };
 
 /* Autotuner: time steps_per_trial batched steps with each tile shape and block

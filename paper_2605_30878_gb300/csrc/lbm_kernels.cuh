@@ -113,6 +113,7 @@ template <> struct PopStore<float> : PlainStore<float> {
     __device__ static void store_units2(float* m, int idx, float va, float vb, float&, float&) {
         *reinterpret_cast<float2*>(m + idx) = make_float2(va, vb);
     }
+    __device__ static void store_zero2(float* m) { *reinterpret_cast<float2*>(m) = make_float2(0.f, 0.f); }
 };
 template <> struct PopStore<__half> {
     static constexpr bool kShift = true, kExact = false;     // moving populations are rounded on store
@@ -186,12 +187,14 @@ constexpr uint32_t MASK_NOT_FLUID = 0x80000000u;
 
 // Block tiles of the step kernels in the shapes the batch autotuner chooses
 // between (V = 0 is the one-node single-domain kernel's tile), in nodes:
-//   V        0        1        2        3        4        5
-//   D3Q19  32x4x2   32x2x4   32x8x1   32x2x2   32x4x4   64x2x2
-//   D2Q9   32x8     64x4     128x2    32x4     32x16    64x4
-//   threads  256      256      256      128      512    128 (float: two nodes each), 256 (FP64)
-// Shape 5 is the tile of the two-node kernel (k_step_pair, PairTile); FP64
-// steps it one node per thread.
+//   V                 0        1        2        3        4        5
+//   D3Q19           32x4x2   32x2x4   32x8x1   32x2x2   32x4x4   64x2x2
+//   D2Q9            32x8     64x4     128x2    32x4     32x16    64x4
+//   threads (float)  128      256      256      64       512      128
+//   threads (FP64)   256      256      256      128      512      256
+// Float arithmetic runs shapes 0, 3 and 5 with the two-node kernel
+// (k_step_pair_batched, PairTile: two x-adjacent nodes per thread); shape 5 is
+// also the tile of the single-domain two-node kernel (k_step_pair).
 constexpr int kTileVariants = 6;
 __host__ __device__ constexpr int tile_extent(int Q, int V, int axis) {
     return V == 5 ? (axis == 0 ? 64 : axis == 1 ? (Q == 9 ? 4 : 2) : (Q == 9 ? 1 : 2))

@@ -224,18 +224,18 @@ void Launch<T, S>::step_batched_v(const int4* tiles, const CUtensorMap* maps, in
                                   cudaStream_t s) {
     using Tl = Tile<Qc, V>;
     const dim3 block(Tl::TX, Tl::TY, Tl::TZ);     // the tile shape, as in the single-domain kernels
-    if constexpr ((V == 5 || V == 3) && sizeof(T) == 4) {
+    if constexpr ((V == 5 || V == 3 || V == 0) && sizeof(T) == 4) {
         // float arithmetic: the two-node kernel over the same tiles, two nodes
-        // per thread (64 nodes wide for shape 5, 32 for shape 3)
-        constexpr int TXn = Tl::TX;
-        using Pt = PairTile<Qc, TXn>;
+        // per thread (64 nodes wide for shape 5, 32 for shapes 0 and 3)
+        constexpr int TXn = Tl::TX, TYn = Tl::TY;
+        using Pt = PairTile<Qc, TXn, TYn>;
         static_assert(Pt::TX == Tl::TX && Pt::TY == Tl::TY && Pt::TZ == Tl::TZ, "the pair tile covers the shape's tile");
         const dim3 pblock(Pt::BX, Pt::TY, Pt::TZ);
         if (ncontrast > 0)
-            k_step_pair_batched<Qc, S, true, TXn><<<ncontrast, pblock, 0, s>>>(tiles, maps, parity);
+            k_step_pair_batched<Qc, S, true, TXn, TYn><<<ncontrast, pblock, 0, s>>>(tiles, maps, parity);
         if (ntiles > ncontrast)
-            k_step_pair_batched<Qc, S, false, TXn><<<ntiles - ncontrast, pblock, 0, s>>>(tiles + ncontrast, maps,
-                                                                                        parity);
+            k_step_pair_batched<Qc, S, false, TXn, TYn><<<ntiles - ncontrast, pblock, 0, s>>>(tiles + ncontrast,
+                                                                                             maps, parity);
     } else {
         if (ncontrast > 0)
             k_step_batched<Qc, T, S, V, true><<<ncontrast, block, 0, s>>>(tiles, maps, parity);

@@ -77,9 +77,9 @@ def test_mixed_batch_matches_the_oracle(precision, Q):
     """Every domain of a mixed batch -- sizes, density ratios 1/10/1000, both
     ghost rules, domains joining at both step parities -- against the FP64
     oracle stepped alone from the same initial state, after each of three legs
-    (tile shape 0 for 1 step, shape 5 -- two nodes per thread in float -- for
-    4, shape 2 for 5; TMA halos on interior tiles, element copies at the y and
-    z ends), within the parity bounds of every precision."""
+    (tile shape 0 for 1 step and shape 5 for 4 -- both two nodes per thread
+    in float --, shape 2 for 5; TMA halos on interior tiles, element copies at
+    the y and z ends), within the parity bounds of every precision."""
     cfgs = _cases(precision, seed=13) if Q == 19 else _mixed_2d(precision)
     doms = _make(cfgs)
     orcs = []
@@ -127,7 +127,7 @@ def test_batch_equals_individual_steps(precision):
     cfgs = _cases(precision)
     alone = _make(cfgs)
     for d in alone:
-        d.step(16)                        # 5 + 4 + 3 + 2 + 2 batched steps
+        d.step(16)                        # 5 + 4 + 3 + 2 + 1 + 1 batched steps
     mixed = _make(cfgs)
     mixed[1].step(1)                      # domains may enter the batch at different parities
     b = lbm.Batch(mixed)
