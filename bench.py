@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-case batched measurement")
     ap.add_argument("--batch-steps", type=int, default=5000, help="timed steps of config 4 (each arm)")
+    ap.add_argument("--batch-cases", type=int, default=64,
+                    help="config 4 over its first this many cases (64: all; fewer for profiling a small batch)")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the served workload (Poisson arrivals at 20/s); 0 skips it")
     ap.add_argument("--serve-plain", action="store_true",
@@ -343,13 +345,13 @@ def batch_cases(seed=2, count=64):
     return out
 
 
-def run_batch_bench(lbm, steps):
+def run_batch_bench(lbm, steps, count=64):
     """Config 4: aggregate MLUPS of the 64 cases advanced in one batch (one
     launch per phase, tile shape autotuned) against a second copy of the same
     cases each stepped by its own launches, for the same number of steps; then
     the contact angle of every case from both copies."""
     import torch
-    cfgs = batch_cases()
+    cfgs = batch_cases()[:count]
 
     def make():
         out = []
@@ -778,7 +780,7 @@ def run_ours(args):
         batched = None
         if world == 1 and not args.no_batch:
             try:
-                batched = run_batch_bench(lbm, args.batch_steps)
+                batched = run_batch_bench(lbm, args.batch_steps, args.batch_cases)
             except Exception as exc:                       # reported in the line, not fatal to it
                 batched = {"error": repr(exc)}
         note("table")
