@@ -1262,12 +1262,14 @@ struct lbm_batch {
     std::vector<int> cur0;             // each domain's buffer parity when the batch was made
     int parity = 0;                    // steps taken by the batch, mod 2
     int variant = 0;
-    // tile shape of the color kernel: 3 (32 x 2 x 2 in 3D, 32 x 2 in 2D),
-    // whatever shape the step kernels use.  The color kernel has no halo, and
-    // narrower tiles leave fewer lanes idle at the ragged x ends of small
-    // domains (config 4: 3.305 ms per step against 3.331 on the step's 64-wide
-    // tiles).  LBM_BATCH_PHI_SHAPE=step: the step's shape; =0..5: that shape.
-    int phi_shape = 3;
+    // tiles of the color kernel, whatever shape the step kernels use (it has
+    // no halo): row chunks of 128 nodes (kPhiRows), which leave only the
+    // padding columns idle.  LBM_BATCH_PHI_SHAPE=step: the step's shape;
+    // =0..5: that shape (shape 3, 32 x 2 x 2, ran config 4 at 3.305 ms per
+    // step against 3.331 on the step's 64-wide tiles).
+    int phi_shape = kPhiRows;
+    int4* phi_rows = nullptr;          // {slot, x0, y0, z} row chunks
+    int nphi_rows = 0;
     int ntiles[kTileVariants] = {};
     int ncontrast[kTileVariants] = {};           // tiles of domains with density contrast come first
     int device = 0;
@@ -1341,8 +1343,10 @@ void batch_launch_step(lbm_batch* b, int parity, cudaStream_t s) {
         using L = decltype(Lx);
         L::ghost_batched(b->GK, b->ghost_tabs, b->ghost_begin, (int)b->doms.size(), b->total_ghosts, s);
         const int Vp = b->phi_shape < 0 ? V : b->phi_shape;
+        const int4* pt = Vp == kPhiRows ? b->phi_rows : b->tiles[Vp];
+        const int np = Vp == kPhiRows ? b->nphi_rows : b->ntiles[Vp];
         L::step_phi_batched(b->Q, V, b->tiles[V], b->maps + (size_t)V * kBatchSlots * 3, b->ntiles[V],
-                            b->ncontrast[V], Vp, b->tiles[Vp], b->ntiles[Vp], parity, s);
+                            b->ncontrast[V], Vp, pt, np, parity, s);
     });
 }
 
@@ -1401,6 +1405,7 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
     b->stream = (cudaStream_t)cuda_stream;
     const char* phi_shape = std::getenv("LBM_BATCH_PHI_SHAPE");
     if (phi_shape && std::strcmp(phi_shape, "step") == 0) b->phi_shape = -1;
+    else if (phi_shape && std::strcmp(phi_shape, "rows") == 0) b->phi_shape = kPhiRows;
     else if (phi_shape && phi_shape[0] >= '0' && phi_shape[0] < '0' + kTileVariants && !phi_shape[1])
         b->phi_shape = phi_shape[0] - '0';
     if (n > kBatchSlots) {
@@ -1470,6 +1475,15 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
                 if (pass == 0) b->ncontrast[V] = (int)tiles[V].size();
             }
         }
+    // row chunks of the color kernel, domain by domain, plane by plane
+    std::vector<int4> rows;
+    for (int i = 0; i < n; ++i) {
+        const lbm_params& P = b->doms[i]->prm;
+        const int64_t px = b->doms[i]->lay.px, per_plane = px * P.ny;
+        for (int z = 0; z < P.nz; ++z)
+            for (int64_t o = 0; o < per_plane; o += kPhiChunk)
+                rows.push_back(make_int4(b->slots[i], (int)(o % px), (int)(o / px), z));
+    }
     b->total_ghosts = gbegin[n];
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t r = off; off = round_up(off + bytes, 256); return r; };
@@ -1483,6 +1497,11 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
         }
         o_t[V] = take(tiles[V].size() * sizeof(int4));
     }
+    if (rows.size() > (size_t)INT32_MAX) {
+        lbm_batch_destroy(b);
+        return bfail(nullptr, LBM_ERR_ARG, "too many tiles");
+    }
+    const size_t o_r = take(rows.size() * sizeof(int4));
     if (cudaMalloc((void**)&b->dev, off) != cudaSuccess) {
         cudaGetLastError();
         lbm_batch_destroy(b);
@@ -1500,6 +1519,11 @@ lbm_status lbm_batch_create(lbm_domain* const* doms, int32_t n, void* cuda_strea
         b->tiles[V] = (int4*)(b->dev + o_t[V]);
         b->ntiles[V] = (int)tiles[V].size();
         e = cudaMemcpy(b->tiles[V], tiles[V].data(), tiles[V].size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {
+        b->phi_rows = (int4*)(b->dev + o_r);
+        b->nphi_rows = (int)rows.size();
+        e = cudaMemcpy(b->phi_rows, rows.data(), rows.size() * sizeof(int4), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {

@@ -196,6 +196,7 @@ constexpr uint32_t MASK_NOT_FLUID = 0x80000000u;
 // (k_step_pair_batched, PairTile: two x-adjacent nodes per thread); shape 5 is
 // also the tile of the single-domain two-node kernel (k_step_pair).
 constexpr int kTileVariants = 6;
+constexpr int kPhiRows = kTileVariants;     // the batch color kernel on row chunks (k_phi_rows_batched)
 __host__ __device__ constexpr int tile_extent(int Q, int V, int axis) {
     return V == 5 ? (axis == 0 ? 64 : axis == 1 ? (Q == 9 ? 4 : 2) : (Q == 9 ? 1 : 2))
          : Q == 9 ? (axis == 0 ? (V == 1 ? 64 : (V == 2 ? 128 : 32))
@@ -1315,6 +1316,26 @@ __global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_phi_batched(const int4*
     // this step's output B* is the buffer the step kernel wrote
     phi_node<Q, T, S>(e.P, e.b[parity].Bout, e.b[parity].mask, e.b[parity].phi, t.y + threadIdx.x, t.z + threadIdx.y,
                       t.w + threadIdx.z, e.b[parity].err);
+}
+
+// Color kernel of a batch over row chunks: a block takes kPhiChunk
+// consecutive nodes of one z plane of one domain in the padded row order
+// (tile {slot, x0, y0, z}: the chunk starts at (x0, y0)), crossing rows where
+// a row ends, so that only the padding columns and a plane's last chunk leave
+// threads idle (box tiles idle at the ragged x end of every row of a small
+// domain), and every pull of the block reads one contiguous run per direction.
+constexpr int kPhiChunk = 128;
+template <int Q, typename T, typename S>
+__global__ void __launch_bounds__(kPhiChunk) k_phi_rows_batched(const int4* __restrict__ tiles, int parity) {
+    const int4 t = __ldg(tiles + (gridDim.x - 1 - blockIdx.x));     // reverse order, as k_phi
+    const BatchEntry<T, S>& e = c_batch<T, S>[idx_checked(t.x, kBatchSlots, c_batch<T, S>[0].b[0].err)];
+    int x = t.y + (int)threadIdx.x, y = t.z;
+    while (x >= e.P.px) {                         // at most kPhiChunk / px + 1 rows on
+        x -= e.P.px;
+        ++y;
+    }
+    if (x >= e.P.nx || y >= e.P.ny) return;       // padding column, or past the plane's end
+    phi_node<Q, T, S>(e.P, e.b[parity].Bout, e.b[parity].mask, e.b[parity].phi, x, y, t.w, e.b[parity].err);
 }
 
 // Ghost tables of all domains: ghost g of the batch belongs to the domain d with

@@ -84,7 +84,8 @@ struct Launch {
     static void step_batched_v(const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast, int parity,
                                cudaStream_t s);
     // step kernels then color kernel of every domain (the ghost update precedes them);
-    // tiles[0, ncontrast) belong to domains with density contrast
+    // tiles[0, ncontrast) belong to domains with density contrast; the color
+    // kernel runs on phi_tiles of shape Vphi, or of row chunks (Vphi == kPhiRows)
     static void step_phi_batched(int Q, int V, const int4* tiles, const CUtensorMap* maps, int ntiles, int ncontrast,
                                  int Vphi, const int4* phi_tiles, int phi_ntiles, int parity, cudaStream_t s);
     // Slot tables: entry_size() bytes per domain, filled by fill_entry, copied

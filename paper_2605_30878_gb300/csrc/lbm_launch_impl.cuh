@@ -272,6 +272,8 @@ void Launch<T, S>::step_phi_batched(int Q, int V, const int4* tiles, const CUten
         if (Vphi == 3) phi(std::integral_constant<int, 3>{});
         if (Vphi == 4) phi(std::integral_constant<int, 4>{});
         if (Vphi == 5) phi(std::integral_constant<int, 5>{});
+        if (Vphi == kPhiRows)
+            k_phi_rows_batched<Qc, T, S><<<phi_ntiles, kPhiChunk, 0, s>>>(phi_tiles, parity);
     };
     if (Q == 9) steps(std::integral_constant<int, 9>{});
     else steps(std::integral_constant<int, 19>{});

@@ -140,6 +140,32 @@ def test_batch_equals_individual_steps(precision):
         for f in ("N", "B", "phi", "u", "p"):
             assert np.array_equal(a.read(f), m.read(f)), (k, f)
 
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16])
+def test_velocity_and_pressure_stay_zero_at_solid_nodes(precision):
+    """The stencils read the previous velocity at solid nodes as 0, so no step
+    kernel may leave anything else there: neither the two-node kernel's lane
+    for a solid partner node nor the zeros it writes around the fluid to fill
+    whole 32-byte sectors (FP32 storage).  Ragged small boxes, stepped alone
+    and batched with every tile shape."""
+    cfgs = _cases(precision)
+    alone, mixed = _make(cfgs), _make(cfgs)
+    for d in alone:
+        d.step(3)
+    b = lbm.Batch(mixed)
+    for v in range(lbm.BATCH_TILE_SHAPES):
+        b.set_variant(v)
+        b.step(1)
+    b.sync()
+    b.close()
+    for c, a, m in zip(cfgs, alone, mixed):
+        solid = c["solid"].reshape(-1) != 0
+        assert solid.any()
+        for d in (a, m):
+            u, p = d.read("u"), d.read("p")
+            assert not np.any(u[:, solid]) and not np.any(p[solid])
+            assert np.any(u[:, ~solid])
+
+
 def test_batch_rejects_outside_steps_and_mixed_precision():
     cfgs = _cases(lbm.FP32, count=2)
     doms = _make(cfgs)
