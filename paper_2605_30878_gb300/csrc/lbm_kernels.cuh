@@ -197,6 +197,7 @@ constexpr uint32_t MASK_NOT_FLUID = 0x80000000u;
 // also the tile of the single-domain two-node kernel (k_step_pair).
 constexpr int kTileVariants = 6;
 constexpr int kPhiRows = kTileVariants;     // the batch color kernel on row chunks (k_phi_rows_batched)
+constexpr int kPhiChunk = 128;              // nodes per block of the color kernels over row chunks
 __host__ __device__ constexpr int tile_extent(int Q, int V, int axis) {
     return V == 5 ? (axis == 0 ? 64 : axis == 1 ? (Q == 9 ? 4 : 2) : (Q == 9 ? 1 : 2))
          : Q == 9 ? (axis == 0 ? (V == 1 ? 64 : (V == 2 ? 128 : 32))
@@ -1324,7 +1325,6 @@ __global__ void __launch_bounds__(Tile<Q, V>::THREADS) k_phi_batched(const int4*
 // a row ends, so that only the padding columns and a plane's last chunk leave
 // threads idle (box tiles idle at the ragged x end of every row of a small
 // domain), and every pull of the block reads one contiguous run per direction.
-constexpr int kPhiChunk = 128;
 template <int Q, typename T, typename S>
 __global__ void __launch_bounds__(kPhiChunk) k_phi_rows_batched(const int4* __restrict__ tiles, int parity) {
     const int4 t = __ldg(tiles + (gridDim.x - 1 - blockIdx.x));     // reverse order, as k_phi
