@@ -156,7 +156,9 @@ size_t lbm_domain_bytes(const lbm_params* params, int64_t n_ghosts);
  * (Fig. 2) and its bilinear (2D) / trilinear (3D) weights over the fluid
  * corners of the cell holding x_F, renormalised; a ghost with no fluid
  * corner uses its fluid stencil neighbour most aligned with n.
- * dev_workspace: NULL to let the library allocate, else a device pointer of
+ * dev_workspace: NULL to let the library allocate (from a memory pool of the
+ * current device that keeps destroyed domains' workspaces for later domains;
+ * see lbm_release_cached_memory), else a device pointer of
  * ws_bytes >= lbm_domain_bytes(...) that the caller keeps alive until
  * lbm_destroy.  cuda_stream: cudaStream_t every device call is issued on
  * (NULL = default stream).  The step kernel copies each tile's color and
@@ -353,8 +355,17 @@ void lbm_batch_destroy(lbm_batch* b);
  * lbm_create_domain when dom is NULL. */
 const char* lbm_last_error(const lbm_domain* dom);
 
-/* Free the domain and any device memory the library allocated. */
+/* Free the domain.  Like cudaFree it first waits for all work on the
+ * device; a workspace the library allocated goes back to the device's
+ * workspace pool (not to the device), ready for the next domain. */
 void lbm_destroy(lbm_domain* dom);
+
+/* Give the memory cached in the workspace pools (workspaces of destroyed
+ * domains) back to the devices, e.g. before other code in the process
+ * allocates device memory.  Waits for all work on those devices.  Not part of
+ * the paper: a memory-management call of this library.  Errors:
+ * LBM_ERR_CUDA. */
+lbm_status lbm_release_cached_memory(void);
 
 #ifdef __cplusplus
 }

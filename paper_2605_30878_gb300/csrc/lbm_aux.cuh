@@ -97,9 +97,15 @@ __global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restric
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     double v = r[a] - ctr[a];
-                    // nearest periodic image; the divide only where one is needed
-                    if ((d.periodic & (1u << a)) && (v > 0.5 * n[a] || v < -0.5 * n[a]))
-                        v -= n[a] * floor(v / n[a] + 0.5);
+                    // nearest periodic image, by whole periods (exact): no FP64
+                    // divide, which this GPU's few FP64 units make the kernel's
+                    // largest cost (the floor form differs only at an exact
+                    // tie, where both images are as near)
+                    if (d.periodic & (1u << a)) {
+                        const double h = 0.5 * n[a];
+                        while (v > h) v -= n[a];
+                        while (v < -h) v += n[a];
+                    }
                     d2 += v * v;
                 }
                 phi[node] = d2 >= out2 ? T(0)

@@ -32,7 +32,7 @@ FIELDS = {"N": 0, "B": 1, "phi": 2, "u": 3, "p": 4}
 EXPORTS = ("lbm_domain_bytes", "lbm_create_domain", "lbm_init_droplet", "lbm_init_phi", "lbm_step", "lbm_sync",
            "lbm_diagnostics", "lbm_read_state", "lbm_write_state", "lbm_profile_steps", "lbm_ghost_table", "lbm_ghost_fallbacks",
            "lbm_launches_per_step", "lbm_bytes_per_fluid_node", "lbm_fluid_nodes", "lbm_last_error", "lbm_destroy",
-           "lbm_phase_sums_noalloc", "lbm_debug_expire_halo_wait", "lbm_debug_bounds_checked",
+           "lbm_release_cached_memory", "lbm_phase_sums_noalloc", "lbm_debug_expire_halo_wait", "lbm_debug_bounds_checked",
            "lbm_debug_plant_bad_index", "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_tune",
            "lbm_batch_variant", "lbm_batch_set_variant", "lbm_batch_launches_per_step", "lbm_batch_last_error",
            "lbm_batch_destroy")
@@ -118,6 +118,8 @@ def load():
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_destroy.argtypes = [C.c_void_p]
     L.lbm_destroy.restype = None
+    L.lbm_release_cached_memory.argtypes = []
+    L.lbm_release_cached_memory.restype = C.c_int
     L.lbm_phase_sums_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64,
                                          C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_char_p,
                                          C.c_size_t]
@@ -207,6 +209,12 @@ def phase_sums_noalloc(dev_class, dev_phi, dev_u, precision, n_components, n_nod
 
 
 _GHOST_DTYPE = np.dtype([("node", "<i8"), ("n", "<f8", (3,))])       # the layout of lbm_ghost
+
+
+def release_cached_memory():
+    """Give the workspaces of destroyed library-allocated domains, which the
+    library keeps for the next domain, back to the devices."""
+    _check(load().lbm_release_cached_memory())
 
 
 def ghost_array(nodes, normals):
