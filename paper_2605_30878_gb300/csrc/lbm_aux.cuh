@@ -84,6 +84,12 @@ __global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restric
     // 1 - |tanh| < 1e-17: the profile is 0 or 1 to double precision there, so
     // tanh (slow on this GPU's few FP64 units) runs only inside that band
     const double far = 10.0 * W, out2 = (R0 + far) * (R0 + far), in2 = R0 > far ? (R0 - far) * (R0 - far) : -1.0;
+    // the same two tests first in FP32, with a margin far above FP32's error
+    // in the squared distance (relative 1e-6): only nodes near the band's
+    // edges or inside it take the FP64 path, whose answer they do not change
+    const float out2f = (float)(out2 * (1.0 + 1e-4) + 1.0);
+    const float in2f = in2 > 0.0 ? (float)(in2 * (1.0 - 1e-4) - 1.0) : -1.0f;
+    const float fc[3] = {(float)cx, (float)cy, (float)cz};
     const int nn = (int)padded_nodes(d);                    // node indices are below 2^31
     for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nn; node += gridDim.x * blockDim.x) {
         const uint8_t c = cls[node];
@@ -93,6 +99,21 @@ __global__ void k_init_phi(Dims d, const uint8_t* __restrict__ cls, T* __restric
                 const double ctr[3] = {cx, cy, cz};
                 const int n[3] = {d.nx, d.ny, d.nz};
                 const int r[3] = {x, y, z};
+                float d2f = 0.0f;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    float v = (float)r[a] - fc[a];
+                    if (d.periodic & (1u << a)) {
+                        const float h = 0.5f * (float)n[a];
+                        while (v > h) v -= (float)n[a];
+                        while (v < -h) v += (float)n[a];
+                    }
+                    d2f = fmaf(v, v, d2f);
+                }
+                if (d2f > out2f || d2f < in2f) {
+                    phi[node] = d2f > out2f ? T(0) : T(1);
+                    continue;
+                }
                 double d2 = 0.0;
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
