@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-case batched measurement")
-    ap.add_argument("--batch-steps", type=int, default=5000, help="timed steps of config 4 (each arm)")
+    ap.add_argument("--batch-steps", type=int, default=5000, help="timed steps of the 64-case batch (each arm)")
     ap.add_argument("--batch-cases", type=int, default=64,
-                    help="config 4 over its first this many cases (64: all; fewer for profiling a small batch)")
+                    help="the 64-case batch over its first this many cases (64: all; fewer for profiling a small batch)")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the served workload (Poisson arrivals at 20/s); 0 skips it")
     ap.add_argument("--serve-plain", action="store_true",
@@ -346,7 +346,7 @@ def batch_cases(seed=2, count=64):
 
 
 def run_batch_bench(lbm, steps, count=64):
-    """Config 4: aggregate MLUPS of the 64 cases advanced in one batch (one
+    """The 64-case batch: aggregate MLUPS of the 64 cases advanced in one batch (one
     launch per phase, tile shape autotuned) against a second copy of the same
     cases each stepped by its own launches, for the same number of steps; then
     the contact angle of every case from both copies."""
@@ -468,7 +468,7 @@ def run_other_storage(lbm, args, cfg, probe, n_angle, fp64_deg):
 
 
 def run_theta_sweep(lbm, n, steps, fp64_steps, storage="fp32"):
-    """Config 2 over its angles: the bench case (density ratio 1000) at theta =
+    """The contact-angle sweep: the bench case (density ratio 1000) at theta =
     30, 60, 90, 120, 150 deg.  Per angle: the line's storage and FP64 from the
     same initial state for `fp64_steps` steps, their contact angles compared
     (the metric's <= 0.5 deg reading: same discretisation, the two
@@ -707,7 +707,7 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        # config 2 over its five angles (FP32 vs FP64 at a fixed step count,
+        # the contact-angle sweep over its five angles (FP32 vs FP64 at a fixed step count,
         # then the line's storage on); the bench case's own angle comes from it
         note("theta sweep")
         sweep = None

@@ -1351,7 +1351,7 @@ struct lbm_batch {
     // tiles of the color kernel, whatever shape the step kernels use (it has
     // no halo): row chunks of 128 nodes (kPhiRows), which leave only the
     // padding columns idle.  LBM_BATCH_PHI_SHAPE=step: the step's shape;
-    // =0..5: that shape (shape 3, 32 x 2 x 2, ran config 4 at 3.305 ms per
+    // =0..5: that shape (shape 3, 32 x 2 x 2, ran a batch of 64 domains of 48^3 to 128^3 at 3.305 ms per
     // step against 3.331 on the step's 64-wide tiles).
     int phi_shape = kPhiRows;
     int4* phi_rows = nullptr;          // {slot, x0, y0, z} row chunks

@@ -145,10 +145,10 @@ __device__ __forceinline__ void step_pair_tile(const StepParams<float>& P, const
     // to its slots when another pair of its group of 8 nodes (32 bytes, one
     // sector of every plane, since planes start at multiples of 64 nodes)
     // stores its update.  The L2 then writes back whole sectors, where a
-    // partly written one would first be read from DRAM (config-4 batch: 10%
-    // less DRAM read per step kernel launch, 6% faster step).  Nothing reads these
-    // slots: a fluid node pulls from fluid nodes or its own slots, and u, p
-    // stay 0 at nodes that are not fluid.  With FP16 storage the extra
+    // partly written one would first be read from DRAM (a batch of 64 domains
+    // of 48^3 to 128^3: 10% less DRAM read per step kernel launch, 6%
+    // faster).  Nothing reads these slots: a fluid node pulls from fluid
+    // nodes or its own slots, and u, p stay 0 at nodes that are not fluid.  With FP16 storage the extra
     // instructions cost more than the traffic saved (its k_step is
     // issue-bound: 0.77 of its roofline with the fill, 0.80 without).
     if constexpr (sizeof(S) == 4) {
