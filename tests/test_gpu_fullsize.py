@@ -1,5 +1,6 @@
-"""Parity at the bench's full size: the D3Q19 192^3 drop on a sphere (density
-ratio 1000), stepped by the same CUDA graphs the bench times, against the FP64
+"""Parity at the bench's full sizes: the D3Q19 192^3 drop on a sphere (density
+ratio 1000) and the 256^3 sphere packing (density ratio 1, 2.3M ghost
+nodes), stepped by the same CUDA graphs the bench times, against the FP64
 oracle on sampled nodes.  The oracle takes the GPU's state after a few steps
 and computes one step at the sampled nodes only (orc_step_sample); the GPU
 advances the same step; the two must agree within the precision's tolerance.
@@ -34,6 +35,7 @@ def _lib():
 
 
 def _samples(cfg, phi, rng):
+    """Random fluid nodes, fluid nodes next to a solid, interface nodes, ghosts."""
     solid = cfg["solid"].reshape(-1)
     fluid = np.flatnonzero(solid == 0)
     # fluid nodes with a solid stencil neighbour: the fluid side of the wall
@@ -44,13 +46,8 @@ def _samples(cfg, phi, rng):
                                      pick(cfg["ghosts"][0], 200)]))
 
 
-@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.FP16])
-def test_bench_case_step_on_sampled_nodes(precision):
-    cfg = wl.sphere_config(n=192, R=32.0, R0=24.0, theta_deg=60.0, rho_ratio=1000.0, mu_ratio=100.0,
-                           precision=precision)
-    g = lbm.Domain(cfg["params"], cfg["solid"], cfg["ghosts"])
-    g.init_droplet(cfg["drop_center"], cfg["R0"])
-    g.step(16)                                   # the 8-step graph, as the bench runs it
+def _check_one_step(cfg, precision, g, label, min_ghosts=50):
+    """The oracle takes g's state, steps the sampled nodes once; g steps once."""
     state = {f: g.read(f) for f in ("N", "B", "phi", "u", "p")}
     rng = np.random.default_rng(11)
     nodes = _samples(cfg, state["phi"], rng)
@@ -83,6 +80,43 @@ def test_bench_case_step_on_sampled_nodes(precision):
     a, b = got["phi"][fl], want["phi"][fl]
     err["phi"] = np.abs(a - b).max() / np.abs(b).max()
     err["phi_ghost"] = np.abs(got["phi"][ghost] - want["phi"][ghost]).max()
-    print("192^3 sampled parity", precision, len(nodes), {k: "%.2e" % v for k, v in err.items()})
+    print(label, precision, len(nodes), {k: "%.2e" % v for k, v in err.items()})
     assert all(v <= TOL[precision] for k, v in err.items() if "own" not in k), err
-    assert ghost.sum() > 50 and fl.sum() > 1500
+    assert ghost.sum() > min_ghosts and fl.sum() > 1500
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.FP16])
+def test_bench_case_step_on_sampled_nodes(precision):
+    cfg = wl.sphere_config(n=192, R=32.0, R0=24.0, theta_deg=60.0, rho_ratio=1000.0, mu_ratio=100.0,
+                           precision=precision)
+    g = lbm.Domain(cfg["params"], cfg["solid"], cfg["ghosts"])
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    g.step(16)                                   # the 8-step graph, as the bench runs it
+    _check_one_step(cfg, precision, g, "192^3 sampled parity")
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def packing():
+    """The bench's 256^3 packing: spheres of radius U(8, 16), porosity 0.45 in
+    x >= 24, seed 1; liquid slab 0 <= x < 16 in the reservoir; theta = 45 deg,
+    density and viscosity ratio 1 (the step kernel without density contrast)."""
+    n = 256
+    c, rad = wl.sphere_packing(n=n)
+    solid, ghosts = wl.packing_domain(c, rad, n=n)
+    x = np.tile(np.arange(n), n * n)
+    d_slab = np.minimum(np.abs(x - 7.5), n - np.abs(x - 7.5))
+    phi0 = wl.tanh_field(8.0 - d_slab, 4.0)
+    P = dict(lattice=19, nx=n, ny=n, nz=n, periodic=7, rho_l=1.0, rho_g=1.0, mu_l=0.1, mu_g=0.1, sigma=0.01,
+             W=4.0, M_phi=0.02, theta=np.radians(45.0))
+    return {"params": P, "solid": solid, "ghosts": ghosts, "phi0": phi0}
+
+
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP16])
+def test_packing_step_on_sampled_nodes(packing, precision):
+    cfg = dict(packing, params=dict(packing["params"], precision=precision))
+    g = lbm.Domain(cfg["params"], cfg["solid"], cfg["ghosts"])
+    g.init_phi(cfg["phi0"])
+    g.step(16)
+    _check_one_step(cfg, precision, g, "256^3 packing sampled parity", min_ghosts=100)
+    g.close()
