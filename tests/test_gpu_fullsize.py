@@ -1,7 +1,8 @@
 """Parity at the bench's full sizes: the D3Q19 192^3 drop on a sphere (density
-ratio 1000) and the 256^3 sphere packing (density ratio 1, 2.3M ghost
-nodes), stepped by the same CUDA graphs the bench times, against the FP64
-oracle on sampled nodes.  The oracle takes the GPU's state after a few steps
+ratio 1000), the 256^3 sphere packing (density ratio 1, 2.3M ghost nodes)
+and two of the paper's Table I grids in D2Q9 (drop on a 1000 x 600 plate and
+on a cylinder in 601 x 601, density ratio 1000), stepped by the same CUDA
+graphs the bench times, against the FP64 oracle on sampled nodes.  The oracle takes the GPU's state after a few steps
 and computes one step at the sampled nodes only (orc_step_sample); the GPU
 advances the same step; the two must agree within the precision's tolerance.
 Samples: random fluid nodes, fluid nodes next to the sphere (bounce-back),
@@ -39,7 +40,7 @@ def _samples(cfg, phi, rng):
     solid = cfg["solid"].reshape(-1)
     fluid = np.flatnonzero(solid == 0)
     # fluid nodes with a solid stencil neighbour: the fluid side of the wall
-    wall = wl.ghost_mask((cfg["solid"] == 0).astype(np.uint8), 19).reshape(-1) & (solid == 0)
+    wall = wl.ghost_mask((cfg["solid"] == 0).astype(np.uint8), cfg["params"]["lattice"]).reshape(-1) & (solid == 0)
     inter = np.flatnonzero((solid == 0) & (phi > 0.05) & (phi < 0.95))
     pick = lambda a, k: rng.choice(a, min(k, len(a)), replace=False) if len(a) else a  # noqa: E731
     return np.unique(np.concatenate([pick(fluid, 1500), pick(np.flatnonzero(wall), 300), pick(inter, 300),
@@ -119,4 +120,37 @@ def test_packing_step_on_sampled_nodes(packing, precision):
     g.init_phi(cfg["phi0"])
     g.step(16)
     _check_one_step(cfg, precision, g, "256^3 packing sampled parity", min_ghosts=100)
+    g.close()
+
+
+def _table1_case(name):
+    """The bench's Table I grids: drop on a plate (walls at y = 0 and ny - 1,
+    periodic x, drop area 1e4 at 500 x 300 scaled with the grid) and on a
+    cylinder (R = 0.2 L at the centre, all periodic); density ratio 1000,
+    viscosity ratio 100, theta = 60 deg."""
+    if name == "plate":
+        nx, ny = 1000, 600
+        solid, ghosts = wl.wall_domain(9, (1, ny, nx), 1, 1)
+        r = np.sqrt(1e4 / np.pi) * nx / 500.0
+        center, periodic = (nx / 2.0, 1.0 + 0.6 * r, 0.0), 1
+    else:
+        nx = ny = 601
+        R = 0.2 * nx
+        solid, ghosts = wl.sphere_domain(9, (1, ny, nx), (nx / 2.0, ny / 2.0, 0.0), R)
+        r = 0.5 * R
+        center, periodic = (nx / 2.0, ny / 2.0 + R + 0.5 * r, 0.0), 7
+    P = dict(lattice=9, nx=nx, ny=ny, nz=1, periodic=periodic, rho_l=1000.0, rho_g=1.0, mu_l=10.0, mu_g=0.1,
+             sigma=0.01, W=4.0, M_phi=0.02, theta=np.radians(60.0))
+    return {"params": P, "solid": solid, "ghosts": ghosts, "drop_center": center, "R0": r}
+
+
+@pytest.mark.parametrize("name", ["plate", "cylinder"])
+@pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.FP16])
+def test_table1_grid_step_on_sampled_nodes(name, precision):
+    base = _table1_case(name)
+    cfg = dict(base, params=dict(base["params"], precision=precision))
+    g = lbm.Domain(cfg["params"], cfg["solid"], cfg["ghosts"])
+    g.init_droplet(cfg["drop_center"], cfg["R0"])
+    g.step(16)
+    _check_one_step(cfg, precision, g, "Table I %s sampled parity" % name)
     g.close()
