@@ -1,8 +1,9 @@
 """Parity at the bench's full sizes: the D3Q19 192^3 drop on a sphere (density
 ratio 1000), the 256^3 sphere packing (density ratio 1, 2.3M ghost nodes)
 and two of the paper's Table I grids in D2Q9 (drop on a 1000 x 600 plate and
-on a cylinder in 601 x 601, density ratio 1000), stepped by the same CUDA
-graphs the bench times, against the FP64 oracle on sampled nodes.  The oracle takes the GPU's state after a few steps
+on a cylinder in 601 x 601, density ratio 1000) and six of the bench's 64
+batched cases stepped by the batch, with the same CUDA graphs the bench
+times, against the FP64 oracle on sampled nodes.  The oracle takes the GPU's state after a few steps
 and computes one step at the sampled nodes only (orc_step_sample); the GPU
 advances the same step; the two must agree within the precision's tolerance.
 Samples: random fluid nodes, fluid nodes next to the sphere (bounce-back),
@@ -47,8 +48,10 @@ def _samples(cfg, phi, rng):
                                      pick(cfg["ghosts"][0], 200)]))
 
 
-def _check_one_step(cfg, precision, g, label, min_ghosts=50):
-    """The oracle takes g's state, steps the sampled nodes once; g steps once."""
+def _oracle_one_step(cfg, g):
+    """The FP64 oracle takes g's state and steps the sampled nodes once:
+    (nodes, the oracle's values there, the u and p rounding budgets)."""
+    precision = cfg["params"]["precision"]
     state = {f: g.read(f) for f in ("N", "B", "phi", "u", "p")}
     rng = np.random.default_rng(11)
     nodes = _samples(cfg, state["phi"], rng)
@@ -58,8 +61,12 @@ def _check_one_step(cfg, precision, g, label, min_ghosts=50):
     want = o.step_sample(nodes)
     # rounding budgets of u and p for one step from this state (parity_util)
     E = dict(zip(("u", "p"), pu.budget(cfg["params"], precision, state, cfg["solid"].reshape(-1) == 0, 1)))
-    del o, state
-    g.step(1)
+    return nodes, want, E
+
+
+def _compare(cfg, g, nodes, want, E, label, min_ghosts=50):
+    """g, stepped once more, against the oracle's step at the sampled nodes."""
+    precision = cfg["params"]["precision"]
     solid = cfg["solid"].reshape(-1)[nodes]
     fl = solid == 0
     ghost = np.isin(nodes, cfg["ghosts"][0])
@@ -84,6 +91,13 @@ def _check_one_step(cfg, precision, g, label, min_ghosts=50):
     print(label, precision, len(nodes), {k: "%.2e" % v for k, v in err.items()})
     assert all(v <= TOL[precision] for k, v in err.items() if "own" not in k), err
     assert ghost.sum() > min_ghosts and fl.sum() > 1500
+
+
+def _check_one_step(cfg, precision, g, label, min_ghosts=50):
+    """The oracle takes g's state, steps the sampled nodes once; g steps once."""
+    nodes, want, E = _oracle_one_step(cfg, g)
+    g.step(1)
+    _compare(cfg, g, nodes, want, E, label, min_ghosts)
 
 
 @pytest.mark.parametrize("precision", [lbm.FP32, lbm.FP64, lbm.FP16])
@@ -154,3 +168,29 @@ def test_table1_grid_step_on_sampled_nodes(name, precision):
     g.step(16)
     _check_one_step(cfg, precision, g, "Table I %s sampled parity" % name)
     g.close()
+
+
+def test_batched_cases_step_on_sampled_nodes():
+    """Six of the bench's 64 batched cases (D3Q19 drop on a sphere, n = 64 to
+    128, density ratios 1 and 10, ragged rows) advanced together by the batch
+    with the 64-wide two-node tiles the tuner picks there, against the FP64
+    oracle on sampled nodes of every domain."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    cfgs = bench.batch_cases()[:6]
+    doms = []
+    for c in cfgs:
+        d = lbm.Domain(c["params"], c["solid"], c["ghosts"])
+        d.init_droplet(c["drop_center"], c["R0"])
+        doms.append(d)
+    b = lbm.Batch(doms)
+    b.set_variant(5)
+    b.step(16)
+    b.sync()
+    ref = [_oracle_one_step(c, d) for c, d in zip(cfgs, doms)]
+    b.step(1)
+    b.sync()
+    for k, (c, d, (nodes, want, E)) in enumerate(zip(cfgs, doms, ref)):
+        _compare(c, d, nodes, want, E, "batched case %d (n = %d, ratio %g)" %
+                 (k, c["params"]["nx"], c["params"]["rho_l"] / c["params"]["rho_g"]))
+    b.close()
