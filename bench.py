@@ -250,13 +250,19 @@ def cores_used():
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
+# device state per grid node of the bench case (populations, fields, tables):
+# 349 B with FP32 storage, 205 B with FP16 storage at 192^3
+STATE_BYTES_PER_NODE = {"fp32": 349.2, "fp16": 205.2}
+
+
 def arm_config(n, theta, storage, world):
-    """The bench line's `config` (both arms)."""
+    """The bench line's `config`, the same in both arms."""
     return {"workload": "D3Q19 %d^3 drop on sphere: sphere R=%g at the centre, drop R0=%g on the +z pole "
                         "at theta=%g deg, rho_l/rho_g=1000, mu_l/mu_g=100, sigma=0.005, %s, periodic"
                         % (n, R_SPHERE * n / N_GRID, R_DROP * n / N_GRID, theta,
                            "FP32" if storage == "fp32" else "FP32 arithmetic, FP16 populations"),
-            "parallelism": "replicas" if world > 1 else "single"}
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (n ** 3 * STATE_BYTES_PER_NODE[storage] / 1e9)}
 
 
 def run_reference(args):
@@ -289,7 +295,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(arm_config(args.n, theta, args.storage, 1), sample_grid=n_ref),
+            "config": arm_config(args.n, theta, args.storage, 1),
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores_used(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -821,8 +827,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if sp == 4 else "f32 (f16 population storage)", "data": "synthetic",
-            "config": dict(arm_config(n, theta, args.storage, world), nodes=nn, fluid_nodes=fluid, ghost_nodes=ng,
-                           l2="inputs larger than L2 (%.2f GB state vs 129 MB L2)" % (lbm.domain_bytes(P, ng) / 1e9)),
+            "config": arm_config(n, theta, args.storage, world),
+            "nodes": {"grid": nn, "fluid": fluid, "ghost": ng, "state_bytes": lbm.domain_bytes(P, ng)},
             "roofline": {"bound": "hbm", "kernel": "k_step_pair<19,%s,contrast>" % ("half" if sp == 2 else "float"),
                          "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
